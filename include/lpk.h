@@ -1,0 +1,228 @@
+/*
+ * lpk.h -- C ABI of the GB300 (sm_103a) library for the interior-point method
+ * of Cui, Morikuni, Tsuchiya and Hayami, "Implementation of interior-point
+ * methods for LP based on Krylov subspace iterative solvers with
+ * inner-iteration preconditioning" (arXiv:1604.07491).
+ *
+ * Problem (Sec. 1, primal-dual pair): min c^T x s.t. A x = b, x >= 0, and its
+ * dual max b^T y s.t. A^T y + s = c, s >= 0, with A an m x n sparse matrix.
+ *
+ * Conventions for every entry point:
+ *  - The caller owns every input and output buffer.  Vector arguments are
+ *    host pointers when on_device == 0 and CUDA device pointers of the
+ *    context's device when on_device != 0 (for instance torch tensors).
+ *  - All vectors are contiguous double arrays in the caller's (natural) row
+ *    and column numbering.  Matrices are CSR with 0-based int32 column
+ *    indices and int64 row pointers.
+ *  - Work is ordered on the context's CUDA stream; every call returns after
+ *    its results are written (the stream is synchronised before return).
+ *  - No call aborts or exits.  Errors are returned as lpk_status and a
+ *    message is available from lpk_last_error().  A context is not
+ *    thread-safe: use one context per host thread.
+ *  - Device-side waits (grid barriers of the persistent kernels) are bounded;
+ *    when a bound is hit the call returns LPK_TIMEOUT and the context stays
+ *    usable.
+ */
+#ifndef LPK_H
+#define LPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+#define LPK_API extern "C"
+#else
+#define LPK_API
+#endif
+
+typedef enum lpk_status {
+  LPK_OK = 0,
+  LPK_MAX_IPM_ITER = 1,           /* interior-point iteration cap (99, Sec. 4.2) hit  */
+  LPK_KRYLOV_STALL = 2,           /* a Krylov solve ended above its tolerance         */
+  LPK_DIVERGED = 3,               /* interior-point iterates became non-finite ('f')  */
+  LPK_BREAKDOWN = 4,              /* Krylov recurrence produced a non-positive divisor */
+  LPK_TIMEOUT = 5,                /* a bounded device-side wait expired               */
+  LPK_EMPTY_ROW_INCONSISTENT = 6, /* empty row i of A with b_i != 0: infeasible       */
+  LPK_EMPTY_COL_UNBOUNDED = 7,    /* empty column j of A with c_j < 0: unbounded      */
+  LPK_INVALID_ARG = 8,            /* bad size, pointer, index or non-finite value     */
+  LPK_OOM = 9,                    /* device allocation failed                         */
+  LPK_CUDA_ERROR = 10             /* a CUDA runtime call failed                       */
+} lpk_status;
+
+/* Krylov method for the search-direction solve (Sec. 3).  MRNE and CGNE are
+ * preconditioned by NE-SSOR inner iterations (Algorithm 5), AB-GMRES by NE-SOR
+ * inner iterations (Algorithm 6). */
+typedef enum lpk_krylov { LPK_MRNE = 0, LPK_CGNE = 1, LPK_ABGMRES = 2 } lpk_krylov;
+
+/* LPK_FP64: everything in double.  LPK_MIXED: the inner sweeps read an FP32
+ * copy of the scaled matrix (4-byte values) and accumulate in double, so the
+ * preconditioner stays a fixed linear (for NE-SSOR, SPD) operator; the w-space
+ * images A_hat^T z, the outer Krylov recurrences, scaling, residuals and step
+ * logic are double. */
+typedef enum lpk_precision { LPK_FP64 = 0, LPK_MIXED = 1 } lpk_precision;
+
+/* Inner sweep kind for lpk_sweep: Algorithm 5 or Algorithm 6. */
+typedef enum lpk_sweep_kind { LPK_NE_SSOR = 0, LPK_NE_SOR = 1 } lpk_sweep_kind;
+
+typedef struct lpk_ctx lpk_ctx;
+typedef struct lpk_problem lpk_problem;
+
+/* Sparse A in CSR.  row_ptr[m+1] (int64, row_ptr[0] = 0, nondecreasing),
+ * col_idx[nnz] (int32 in [0, n)), val[nnz] (finite doubles).  Duplicate
+ * (row, column) pairs are rejected.  on_device selects host or device
+ * pointers for the three arrays. */
+typedef struct lpk_matrix {
+  int32_t m, n;
+  int64_t nnz;
+  const int64_t *row_ptr;
+  const int32_t *col_idx;
+  const double *val;
+  int32_t on_device;
+  int32_t reserved;
+} lpk_matrix;
+
+/* Options of lpk_lp_solve.  Defaults (lpk_default_options) follow Sec. 2.1
+ * and Sec. 4.2: tol = 1e-8 (eps_out), eta = 0.9995 in [0.9, 1), phi = 1e-5,
+ * sigma_max = 0.208, eps_in0 = 1e-6 (clamped to [1e-14, 1e-4]), max_ipm = 99,
+ * max_krylov = 0 (means m).  inner_sweeps (ell) and omega are the inner
+ * iteration parameters (odd ell keeps the NE-SSOR preconditioner SPD,
+ * Sec. 3.3). */
+typedef struct lpk_options {
+  double tol;
+  double eta;
+  double phi;
+  double sigma_max;
+  double eps_in0;
+  double omega;
+  double start_tol;   /* Krylov tolerance of the two starting-point solves */
+  double backtrack;   /* shrink factor of the centrality backtracking       */
+  int32_t max_ipm;
+  int32_t max_krylov;
+  int32_t inner_sweeps;
+  int32_t solver;     /* lpk_krylov    */
+  int32_t precision;  /* lpk_precision */
+  int32_t verbose;    /* 1: one line per interior-point iteration on stderr */
+  uint64_t color_seed;
+} lpk_options;
+
+/* Result summary of lpk_lp_solve.  gamma is the error measure of
+ * Eq. (errorMeasureDef); pinf = ||b - Ax|| / max(||b||, 1),
+ * dinf = ||c - A^T y - s|| / max(||c||, 1),
+ * rel_gap = |c^T x - b^T y| / (1 + |c^T x|). */
+typedef struct lpk_info {
+  int32_t status;
+  int32_t ipm_iters;
+  int64_t krylov_iters_total;
+  int32_t n_colors;
+  int32_t krylov_failures;
+  double gamma, rel_gap, pinf, dinf, mu, obj_primal, obj_dual;
+  double solve_ms;
+} lpk_info;
+
+/* Result of one Krylov solve: iterations over all restarts, whether the
+ * explicit scaled residual ||f_hat - A_hat dw|| <= tol ||f_hat|| holds, and
+ * both residual norms. */
+typedef struct lpk_krylov_info {
+  int32_t iters;
+  int32_t converged;
+  int32_t restarts;
+  int32_t breakdown;
+  double res0;
+  double res;
+} lpk_krylov_info;
+
+/* Counters of one context since its creation or the last lpk_reset_stats:
+ * every kernel launch the library issued, and for the persistent Krylov
+ * kernel (the dominant kernel) its launches, their device time measured with
+ * CUDA events on the context stream, the Krylov iterations, inner-sweep
+ * passes (one forward or backward pass over all colors), FP64 row passes
+ * over A_hat (products and residuals) and CSC passes (w-space images). */
+typedef struct lpk_stats {
+  int64_t launches;
+  int64_t krylov_launches;
+  double krylov_ms;
+  int64_t krylov_iters;
+  int64_t sweep_passes;
+  int64_t row_passes;
+  int64_t csc_passes;
+  int64_t barriers;
+} lpk_stats;
+
+/* Create a context on CUDA device `device`, ordered on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The context owns its
+ * device workspace; the stream stays owned by the caller. */
+LPK_API lpk_status lpk_create(lpk_ctx **ctx, int32_t device, void *cuda_stream);
+LPK_API void lpk_destroy(lpk_ctx *ctx);
+LPK_API const char *lpk_last_error(const lpk_ctx *ctx);
+LPK_API void lpk_default_options(lpk_options *opt);
+LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out);
+LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx);
+
+/* Copy A to the device, validate it, remove empty rows and columns (the only
+ * preprocessing of Sec. 4.2) and compute the multicolor row order on the
+ * device: rows are colored greedily in decreasing priority
+ * splitmix64(color_seed ^ row), each taking the smallest color not used by a
+ * higher-priority row sharing a column, so rows of one color share no column
+ * and NE-(S)SOR can update them in parallel (the paper sweeps rows in natural
+ * order, Algorithms 5-6).  The problem owns device copies of A (permuted CSR,
+ * CSC, scaled FP64 and FP32 values) and is immutable afterwards. */
+LPK_API lpk_status lpk_prepare(lpk_ctx *ctx, const lpk_matrix *A, uint64_t color_seed,
+                               lpk_problem **P);
+/* Frees a problem.  Destroying a context releases the device memory of its
+ * remaining problems; their handles must then still be passed to
+ * lpk_problem_free (which only releases the host handle) and nothing else. */
+LPK_API void lpk_problem_free(lpk_problem *P);
+
+/* Sizes of the prepared problem: m, n, nnz of the input and the number of
+ * colors.  Any output pointer may be NULL. */
+LPK_API lpk_status lpk_problem_dims(const lpk_problem *P, int32_t *m, int32_t *n, int64_t *nnz,
+                                    int32_t *n_colors);
+
+/* Copy the coloring to host arrays: color[m] (color of each input row; -1 for
+ * a removed empty row), color_ptr[n_colors+1] and perm[m'] (kept rows in
+ * sweep order, input numbering).  Any output pointer may be NULL. */
+LPK_API lpk_status lpk_problem_coloring(lpk_ctx *ctx, const lpk_problem *P, int32_t *color,
+                                        int32_t *perm, int32_t *color_ptr);
+
+/* Row scaling of Sec. 3.5 for D = diag(sqrt(d2)): rho[i] = ||(A D)_i||_2 and
+ * ahat[k] = a_k sqrt(d2_col(k)) / rho_row(k) in the input CSR order.  d2[n]
+ * > 0; rho[m]; ahat[nnz]. ahat may be NULL. */
+LPK_API lpk_status lpk_scale_rows(lpk_ctx *ctx, lpk_problem *P, const double *d2, double *rho,
+                                  double *ahat, int32_t on_device);
+
+/* y = A x (transpose == 0; x[n], y[m]) or y = A^T x (transpose != 0; x[m],
+ * y[n]) with the unscaled A, in double. */
+LPK_API lpk_status lpk_spmv(lpk_ctx *ctx, lpk_problem *P, int32_t transpose, const double *x,
+                            double *y, int32_t on_device);
+
+/* Inner iterations on the row-scaled matrix A_hat = D_cal^-1 A D (Sec. 3.5,
+ * unit row norms), rows visited in the multicolor order:
+ *  LPK_NE_SSOR (Algorithm 5): z[m] = C^<ell> g, u[n] = A_hat^T z.
+ *  LPK_NE_SOR  (Algorithm 6): u[n] = B^<ell> g, z[m] = the accumulated row
+ *                             corrections, u = A_hat^T z.
+ * g[m] is in the scaled space.  precision LPK_MIXED runs the sweep in FP32. */
+LPK_API lpk_status lpk_sweep(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *g,
+                             int32_t kind, int32_t inner_sweeps, double omega, int32_t precision,
+                             double *z, double *u, int32_t on_device);
+
+/* Search-direction solve of Sec. 2.2: A diag(d2) A^T dy = f through the
+ * minimum-norm problem min ||dw|| s.t. A D dw = f, D = diag(sqrt(d2))
+ * (Eq. minnrmprob), row-scaled (Sec. 3.5), solved by `solver` (Algorithms
+ * 2-4) with `inner_sweeps` inner iterations of relaxation `omega`, to the
+ * scaled tolerance ||f_hat - A_hat dw|| <= tol ||f_hat|| or max_iter
+ * iterations (0 -> m).  Outputs dy[m] and dw[n] = D A^T dy (dw may be NULL);
+ * for rank-deficient A, dy is the one the iteration reaches from dy = 0.
+ * kinfo may be NULL.  Returns LPK_OK even when the tolerance is not reached
+ * (kinfo->converged tells). */
+LPK_API lpk_status lpk_ne_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *f,
+                                int32_t inner_sweeps, double omega, int32_t solver,
+                                int32_t precision, double tol, int32_t max_iter, double *dy,
+                                double *dw, lpk_krylov_info *kinfo, int32_t on_device);
+
+/* Interior-point solve (Algorithm 1 with the w-recurrence of Sec. 2.2): b[m],
+ * c[n] in; x[n], y[m], s[n] out.  opt may be NULL (defaults).  info may be
+ * NULL.  Returns LPK_OK when Gamma <= tol and rel_gap <= tol. */
+LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, const double *c,
+                                const lpk_options *opt, double *x, double *y, double *s,
+                                lpk_info *info, int32_t on_device);
+
+#endif /* LPK_H */

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  Tolerances:
+  * coloring, permutation: bit-exact;
+  * row scaling, SpMV: 1e-13 relative (FP64, different summation order);
+  * FP64 sweeps: 1e-11 relative in norm (same row order, per-row dot products
+    summed in a different order; the sweep is a contraction so rounding does
+    not grow beyond a few ulps per row visit);
+  * FP32 sweeps: 2e-4 relative in norm (FP32 unit roundoff 6e-8 times row
+    lengths up to 200 and ell <= 3 passes of accumulated updates);
+  * Krylov solves: both sides must satisfy their residual bound; the solutions
+    must agree to (tolerance x condition) as stated per test;
+  * LP solves: relative objective error <= 1e-7, pinf, dinf, rel-gap <= 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1604_07491_gb300 import gen  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lpk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07491_gb300 import build, lpk as L
+    build.build()
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lpk):
+    c = lpk.Context(0)
+    yield c
+    c.close()
+
+
+def certs(lp, x, y, s):
+    A = lp.scipy()
+    pinf = np.linalg.norm(lp.b - A @ x) / max(np.linalg.norm(lp.b), 1)
+    dinf = np.linalg.norm(lp.c - A.T @ y - s) / max(np.linalg.norm(lp.c), 1)
+    gap = abs(lp.c @ x - lp.b @ y) / (1 + abs(lp.c @ x))
+    return pinf, dinf, gap
+
+
+LPS = {
+    "tiny": lambda: gen.tiny_lp(),
+    "medium_0.05": lambda: gen.medium_lp(0.05),
+    "medium_0.0123": lambda: gen.medium_lp(0.0123),   # ragged sizes (m = 246)
+    "assignment": lambda: gen.assignment_lp(),
+}
+
+
+@pytest.mark.parametrize("name", list(LPS) + ["large_0.1"])
+def test_coloring_bit_exact(lpk, ctx, orc, name):
+    lp = gen.large_lp(0.1) if name == "large_0.1" else LPS[name]()
+    P = lpk.Problem.from_lp(ctx, lp, color_seed=0xC0FFEE)
+    color, perm, cptr = P.coloring()
+    nc, ocolor, operm, ocptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 0xC0FFEE)
+    assert P.n_colors == nc
+    assert np.array_equal(color, ocolor)
+    assert np.array_equal(perm, operm)
+    assert np.array_equal(cptr, ocptr)
+
+
+def test_coloring_device_input_full_medium(lpk, ctx, orc):
+    lp = gen.medium_lp()
+    P = lpk.Problem.from_lp(ctx, lp, device="cuda")
+    color, perm, cptr = P.coloring()
+    nc, ocolor, operm, ocptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 0x5EED)
+    assert np.array_equal(color, ocolor) and np.array_equal(perm, operm)
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium_0.05"])
+def test_scaling_and_spmv(lpk, ctx, orc, name):
+    lp = LPS[name]()
+    P = lpk.Problem.from_lp(ctx, lp)
+    rng = np.random.default_rng(1)
+    d2 = np.exp(rng.uniform(-10, 10, lp.n))
+    rho, ahat = P.scale_rows(d2, with_ahat=True)
+    oahat, orho = orc.scale_rows(lp.m, lp.row_ptr, lp.col_idx, lp.val, d2)
+    assert np.allclose(rho, orho, rtol=1e-13, atol=0)
+    assert np.allclose(ahat, oahat, rtol=1e-13, atol=1e-300)
+    A = lp.scipy()
+    x = rng.standard_normal(lp.n)
+    y = rng.standard_normal(lp.m)
+    assert np.allclose(P.spmv(x), A @ x, rtol=1e-13, atol=1e-13 * np.abs(A @ x).max())
+    assert np.allclose(P.spmv(y, transpose=True), A.T @ y, rtol=1e-13,
+                       atol=1e-13 * np.abs(A.T @ y).max())
+    # device tensors in, device tensors out
+    xt = torch.from_numpy(x).cuda()
+    assert np.allclose(P.spmv(xt).cpu().numpy(), A @ x, rtol=1e-13, atol=1e-13 * np.abs(A @ x).max())
+
+
+def _oracle_sweep(orc, lp, perm, d2, g, kind, ell, omega):
+    ahat, rho = orc.scale_rows(lp.m, lp.row_ptr, lp.col_idx, lp.val, d2)
+    if kind == 0:
+        return orc.nessor(lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, g, ell, omega)
+    z, y = orc.nesor(lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, g, ell, omega)
+    return y, z    # (row corrections m, w-space n) as the C ABI returns them
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium_0.0123", "assignment", "medium_full"])
+@pytest.mark.parametrize("kind,ell,omega", [(0, 1, 1.0), (0, 3, 1.2), (1, 2, 0.9)])
+def test_sweep_parity(lpk, ctx, orc, name, kind, ell, omega):
+    lp = gen.medium_lp() if name == "medium_full" else LPS[name]()
+    P = lpk.Problem.from_lp(ctx, lp)
+    color, perm, cptr = P.coloring()
+    rng = np.random.default_rng(2)
+    d2 = np.exp(rng.uniform(-6, 6, lp.n))
+    g = rng.standard_normal(lp.m)
+    oz, ou = _oracle_sweep(orc, lp, perm, d2, g, kind, ell, omega)
+    z, u = P.sweep(d2, g, kind=kind, inner_sweeps=ell, omega=omega, precision=lpk.FP64)
+    assert rel(z, oz) < 1e-11 and rel(u, ou) < 1e-11
+    z32, u32 = P.sweep(d2, g, kind=kind, inner_sweeps=ell, omega=omega, precision=lpk.MIXED)
+    assert rel(z32, oz) < 2e-4 and rel(u32, ou) < 2e-4
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "medium_0.05", "assignment"])
+def test_ne_solve_parity(lpk, ctx, orc, name, solver):
+    lp = LPS[name]()
+    P = lpk.Problem.from_lp(ctx, lp)
+    color, perm, cptr = P.coloring()
+    rng = np.random.default_rng(3)
+    d2 = np.exp(rng.uniform(-3, 3, lp.n))
+    A = lp.scipy()
+    f = A @ (d2 * rng.standard_normal(lp.n))
+    tol = 1e-9
+    ell = 3 if name == "assignment" else 1
+    ody, odw, oinfo = orc.ne_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, f, ell, 1.0,
+                                   solver, tol, 20 * lp.m)
+    dy, dw, info = P.ne_solve(d2, f, inner_sweeps=ell, solver=solver, tol=tol, max_iter=20 * lp.m)
+    assert oinfo["converged"] and info["converged"]
+    assert abs(info["iters"] - oinfo["iters"]) <= max(2, oinfo["iters"] // 20)
+    # both are the minimum-norm solution to the tolerance: dw agrees closely and
+    # is consistent with dy (dw = D A^T dy)
+    assert rel(dw, odw) < 1e-5
+    assert rel(dw, np.sqrt(d2) * (A.T @ dy)) < 1e-9
+    r = f - A @ (d2 * (A.T @ dy))
+    assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(f)
+
+
+def _lp_case(name):
+    if name == "tiny":
+        return gen.tiny_lp(), dict(inner_sweeps=1)
+    if name == "assignment":
+        return gen.assignment_lp(), dict(inner_sweeps=3)
+    if name == "medium_0.05":
+        lp = gen.medium_lp(0.05)
+        return lp, dict(inner_sweeps=3, max_krylov=3 * lp.m)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "assignment", "medium_0.05"])
+def test_lp_solve_parity(lpk, ctx, orc, name, precision):
+    lp, kw = _lp_case(name)
+    P = lpk.Problem.from_lp(ctx, lp)
+    x, y, s, info = P.lp_solve(lp.b, lp.c, precision=precision, **kw)
+    assert info["status_name"] == "OK", info
+    ox, oy, os_, oinfo = orc.lp_solve_lp(lp, **kw)
+    assert oinfo["status_name"] == "OK"
+    ref = oinfo["obj_primal"]
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
+    pinf, dinf, gap = certs(lp, x, y, s)
+    assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+    if name == "tiny":   # unique optimum: vectors agree too
+        assert rel(x, ox) < 1e-6
+
+
+def test_lp_solve_device_tensors_and_determinism(lpk, ctx):
+    lp = gen.tiny_lp()
+    P = lpk.Problem.from_lp(ctx, lp, device="cuda")
+    b = torch.from_numpy(lp.b).cuda()
+    c = torch.from_numpy(lp.c).cuda()
+    r1 = P.lp_solve(b, c)
+    r2 = P.lp_solve(b, c)
+    assert r1[3]["status_name"] == "OK"
+    for a, bb in zip(r1[:3], r2[:3]):
+        assert a.is_cuda and torch.equal(a, bb)
+
+
+def test_empty_rows_cols_and_errors(lpk, ctx, orc):
+    import scipy.sparse as sp
+    lp = gen.tiny_lp()
+    A = lp.scipy().toarray()
+    A2 = np.zeros((lp.m + 1, lp.n + 1))
+    A2[1:, :lp.n] = A
+    b2 = np.concatenate([[0.0], lp.b])
+    c2 = np.concatenate([lp.c, [3.0]])
+    S = sp.csr_matrix(A2)
+    rp, ci = S.indptr.astype(np.int64), S.indices.astype(np.int32)
+    P = lpk.Problem(ctx, lp.m + 1, lp.n + 1, rp, ci, S.data)
+    x, y, s, info = P.lp_solve(b2, c2)
+    assert info["status_name"] == "OK"
+    ox, oy, os_, oinfo = orc.lp_solve(lp.m + 1, lp.n + 1, rp, ci, S.data, b2, c2)
+    assert abs(info["obj_primal"] - oinfo["obj_primal"]) <= 1e-7 * abs(oinfo["obj_primal"])
+    assert x[-1] == 0.0 and s[-1] == 3.0 and y[0] == 0.0
+    b3 = b2.copy()
+    b3[0] = 1.0
+    with pytest.raises(lpk.LpkError) as e:
+        P.lp_solve(b3, c2)
+    assert e.value.status == lpk.EMPTY_ROW_INCONSISTENT
+    c3 = c2.copy()
+    c3[-1] = -1.0
+    with pytest.raises(lpk.LpkError) as e:
+        P.lp_solve(b2, c3)
+    assert e.value.status == lpk.EMPTY_COL_UNBOUNDED
+    bad = ci.copy()
+    bad[3] = lp.n + 5
+    with pytest.raises(lpk.LpkError) as e:
+        lpk.Problem(ctx, lp.m + 1, lp.n + 1, rp, bad, S.data)
+    assert e.value.status == lpk.INVALID_ARG
+    with pytest.raises(lpk.LpkError):
+        P.ne_solve(-np.ones(lp.n + 1), np.ones(lp.m + 1))
+
+
+def test_full_size_medium_sampled(lpk, ctx, orc):
+    """Full-size medium LP in the launch configuration the benchmark uses: the
+    first ne_solve of the interior-point method's starting point (D = I) is
+    checked against the oracle's; plus one mixed sweep per color sampled."""
+    lp = gen.medium_lp()
+    P = lpk.Problem.from_lp(ctx, lp, device="cuda")
+    color, perm, cptr = P.coloring()
+    d2 = np.ones(lp.n)
+    ody, odw, oinfo = orc.ne_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, lp.b, 3,
+                                   1.0, 0, 1e-8, lp.m)
+    dy, dw, info = P.ne_solve(torch.from_numpy(d2).cuda(), torch.from_numpy(lp.b).cuda(),
+                              inner_sweeps=3, tol=1e-8)
+    assert info["converged"] and oinfo["converged"]
+    assert abs(info["iters"] - oinfo["iters"]) <= 2
+    assert rel(dw.cpu().numpy(), odw) < 1e-5
