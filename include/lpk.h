@@ -145,7 +145,19 @@ typedef struct lpk_stats {
   int64_t row_passes;
   int64_t csc_passes;
   int64_t barriers;
+  int32_t last_cluster_size;  /* 0: the last Krylov launch used the grid path */
+  int32_t reserved;
 } lpk_stats;
+
+/* Execution path of the persistent Krylov kernel.
+ *  LPK_EXEC_AUTO:    one thread-block cluster (hardware cluster barrier, u in
+ *                    distributed shared memory) when u fits in 16 CTAs' shared
+ *                    memory, else the grid path.
+ *  LPK_EXEC_GRID:    every SM, software grid barrier, u in global memory.
+ *  LPK_EXEC_CLUSTER: the cluster path (LPK_INVALID_ARG at solve time if u does
+ *                    not fit).
+ * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
+typedef enum lpk_exec { LPK_EXEC_AUTO = 0, LPK_EXEC_GRID = 1, LPK_EXEC_CLUSTER = 2 } lpk_exec;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  The context owns its
@@ -156,6 +168,7 @@ LPK_API const char *lpk_last_error(const lpk_ctx *ctx);
 LPK_API void lpk_default_options(lpk_options *opt);
 LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out);
 LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx);
+LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size);
 
 /* Copy A to the device, validate it, remove empty rows and columns (the only
  * preprocessing of Sec. 4.2) and compute the multicolor row order on the

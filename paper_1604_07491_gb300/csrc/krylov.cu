@@ -1,14 +1,20 @@
-// krylov.cu -- persistent cooperative kernels for the search-direction solve
-// (Sec. 3): CGNE (Algorithm 2) and MRNE (Algorithm 3) with NE-SSOR inner
-// iterations (Algorithm 5), plus a sweep-only mode for NE-SSOR / NE-SOR
-// (Algorithm 6).  One launch runs a whole Krylov solve: no host round trip per
-// iteration.
+// krylov.cu -- persistent kernels for the search-direction solve (Sec. 3):
+// CGNE (Algorithm 2) and MRNE (Algorithm 3) with NE-SSOR inner iterations
+// (Algorithm 5), plus a sweep-only mode for NE-SSOR / NE-SOR (Algorithm 6).
+// One launch runs a whole Krylov solve: no host round trip per iteration.
 //
-// Phases are separated by a software grid barrier (monotonic arrival counter,
-// bounded wait on %globaltimer; on expiry the kernel records LPK_TIMEOUT and
-// every CTA returns).  Reductions are two-stage and deterministic: each CTA
-// writes its partial, and after the barrier every CTA sums all partials in
-// CTA order, so all CTAs take identical control decisions.
+// The kernel body is written once over a group policy:
+//  * GridGrp: every SM, one CTA each (cooperative launch); phases are
+//    separated by a software grid barrier (monotonic arrival counter, bounded
+//    wait on %globaltimer: on expiry the kernel records LPK_TIMEOUT and every
+//    CTA returns); the sweep vector u lives in global memory (L2).
+//  * ClusterGrp: one thread-block cluster (up to 16 CTAs on one GPC); phases
+//    are separated by the hardware cluster barrier and u lives in the CTAs'
+//    shared memory (distributed shared memory, 2^s entries per CTA), so the
+//    gather/scatter of a sweep row never leaves the GPC.
+// Reductions are two-stage and deterministic: each CTA writes its partial,
+// and after the barrier every CTA sums all partials in CTA order, so all CTAs
+// take identical control decisions.
 //
 // Inner sweep.  Rows are stored color by color; the rows of one color share
 // no column, so a warp per row computes d_i = omega (g_i - (alpha_i, u))
@@ -28,24 +34,33 @@
 //  The p (MRNE) and q (CGNE) updates are fused into the next product: the
 //  product gathers q + beta p_old inline while the new p is written to a
 //  second buffer, saving one barrier per iteration.
+// Mixed precision (wy): the sweeps read the FP32 copy of A_hat and accumulate
+// in FP64; the w-space images v = A_hat^T vt are recomputed by an FP64 CSC
+// product so dw and dy stay consistent to FP64 rounding.
+#include <cooperative_groups.h>
+
 #include <cstdio>
 
 #include "lpk_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace {
 
-constexpr int KTPB = 512;
+constexpr int KTPB = 256;
 constexpr int KWPB = KTPB / 32;
 constexpr int RC = 4;                 // row entries per lane kept in registers
 constexpr unsigned long long TIMEOUT_NS = 5000000000ull;  // 5 s per barrier wait
+constexpr int MAX_CLUSTER = 16;
+constexpr int MAX_SHIFT = 14;         // <= 2^14 doubles (128 KB) of u per CTA
 
 enum { M_MRNE = 0, M_CGNE = 1, M_SWEEP = 7, M_SWEEP_SSOR = 8, M_SWEEP_SOR = 9 };
-enum { EXIT_CONV = 0, EXIT_MAXIT = 1, EXIT_BREAK = 2, EXIT_STALL = 3 };
+enum { EXIT_CONV = 0, EXIT_MAXIT = 1, EXIT_BREAK = 2 };
 
 struct KrylovCtl {
   unsigned long long bar;
   int status;
-  int iters, restarts, converged, breakdown, iters32, escalations;
+  int iters, restarts, converged, breakdown, pad;
   double res0, res;
   long long passes, rows, cols, barriers;   // work counters of the launch
 };
@@ -58,8 +73,6 @@ struct KArgs {
   const int *cp, *ri;              // CSC of A_hat (rows are sweep positions)
   const double *aht;               // A_hat values in CSC order
   int wy;                          // mixed precision: w-space images by FP64 CSC products
-  int f32;                         // inner sweeps start in FP32
-  int stall;                       // FP32 phase ends after this many iterations without a new best
   double *uw;                      // n-space workspace of the CGNE wy path
   int ell;
   double omega;
@@ -67,17 +80,18 @@ struct KArgs {
   double tol;
   int maxit;
   int method;
-  double cycle_tol;                // a cycle ends at ||g|| <= cycle_tol * ||g at cycle start||
   int max_restarts;
+  int u_shift;                     // cluster mode: 2^u_shift entries of u per CTA
+  int rw;                          // z slots per warp in shared memory
+  int z_off;                       // byte offset of the z slots in dynamic shared memory
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
-  void *u, *z;                     // sweep state: u (n), z (m), TI
-  double *part;                    // [8 * gridDim]
+  double *u, *z;                   // sweep state: u (n, grid mode), z (m)
+  double *part;                    // [8 * CTAs]
   KrylovCtl *ctl;
   double *hist;
-  // sweep-only mode outputs
-  double *out_z, *out_u;
+  double *out_z, *out_u;           // sweep-only mode outputs
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -96,19 +110,22 @@ struct Counters {
   long long passes = 0, rows = 0, cols = 0;
 };
 
-struct GridBar {
+// ---- group policies --------------------------------------------------------
+struct GridGrp {
   unsigned long long *cnt;
   int *status;
   unsigned long long epoch;
-  unsigned nblk;
-  // returns false if the wait timed out or another CTA reported a failure
+  double *u;
+  __device__ __forceinline__ unsigned rank() const { return blockIdx.x; }
+  __device__ __forceinline__ unsigned size() const { return gridDim.x; }
   // The CTA barrier orders this CTA's writes before thread 0's release-add;
   // the acquire poll orders every later read after all CTAs' writes.
+  // Returns false if the wait timed out or another CTA reported a failure.
   __device__ __forceinline__ bool sync(int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
       epoch += 1;
-      const unsigned long long target = epoch * (unsigned long long)nblk;
+      const unsigned long long target = epoch * (unsigned long long)gridDim.x;
       asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
       int ok = 1;
       unsigned it = 0;
@@ -126,155 +143,332 @@ struct GridBar {
     __syncthreads();
     return *s_ok != 0;
   }
+  // split form: arrive, independent work (prefetch), wait
+  __device__ __forceinline__ void arrive() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      epoch += 1;
+      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
+    }
+  }
+  __device__ __forceinline__ bool wait(int *s_ok) {
+    if (threadIdx.x == 0) {
+      const unsigned long long target = epoch * (unsigned long long)gridDim.x;
+      int ok = 1;
+      unsigned it = 0;
+      unsigned long long t0 = 0;
+      while (ld_acquire(cnt) < target) {
+        if ((++it & 255u) == 0u) {
+          if (*(volatile int *)status != 0) { ok = 0; break; }
+          unsigned long long now = globaltimer();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > TIMEOUT_NS) { atomicCAS(status, 0, (int)LPK_TIMEOUT); ok = 0; break; }
+        }
+      }
+      *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+  }
+  __device__ __forceinline__ long long barriers() const { return (long long)epoch; }
+  __device__ __forceinline__ double uld(int j) const { return __ldcg(u + j); }
+  __device__ __forceinline__ void ust(int j, double v) const { u[j] = v; }
+  __device__ __forceinline__ void uzero(int n) const {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) u[j] = 0.0;
+  }
+};
+
+struct ClusterGrp {
+  double *u_sm;      // this CTA's slice of u (shared memory)
+  unsigned shift, mask, rank_, size_;
+  long long epoch;
+  __device__ __forceinline__ unsigned rank() const { return rank_; }
+  __device__ __forceinline__ unsigned size() const { return size_; }
+  // hardware cluster barrier: arrive has release and wait acquire semantics
+  // at cluster scope, for shared and global memory alike
+  __device__ __forceinline__ bool sync(int *) {
+    cg::this_cluster().sync();
+    ++epoch;
+    return true;
+  }
+  // split form: the release arrive waits only for this thread's earlier
+  // accesses; loads issued between arrive and wait overlap the barrier
+  __device__ __forceinline__ void arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    ++epoch;
+  }
+  __device__ __forceinline__ bool wait(int *) {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    return true;
+  }
+  __device__ __forceinline__ long long barriers() const { return epoch; }
+  __device__ __forceinline__ double *up(int j) const {
+    return cg::this_cluster().map_shared_rank(u_sm, j >> shift) + (j & mask);
+  }
+  __device__ __forceinline__ double uld(int j) const { return *(volatile double *)up(j); }
+  __device__ __forceinline__ void ust(int j, double v) const { *up(j) = v; }
+  __device__ __forceinline__ void uzero(int) const {
+    for (unsigned i = threadIdx.x; i <= mask; i += blockDim.x) u_sm[i] = 0.0;
+  }
 };
 
 // CTA partial sums -> part[k * G + rank] (thread 0 writes)
-template <int K>
-__device__ __forceinline__ void put_partials(double (&v)[K], double *part, double *sred) {
+template <int K, typename GRP>
+__device__ __forceinline__ void put_partials(const GRP &Gp, double (&v)[K], double *part, double *sred) {
   block_sum<K>(v, sred);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+    for (int k = 0; k < K; ++k) part[k * Gp.size() + Gp.rank()] = v[k];
   }
 }
 // after a barrier: every CTA sums the G partials of slots [0, K) in CTA order
-template <int K>
-__device__ __forceinline__ void get_sums(double (&v)[K], const double *part, double *sred) {
+template <int K, typename GRP>
+__device__ __forceinline__ void get_sums(const GRP &Gp, double (&v)[K], const double *part, double *sred) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = threadIdx.x < gridDim.x ? __ldcg(&part[k * gridDim.x + threadIdx.x]) : 0.0;
+  for (int k = 0; k < K; ++k) v[k] = threadIdx.x < Gp.size() ? __ldcg(&part[k * Gp.size() + threadIdx.x]) : 0.0;
   block_sum<K>(v, sred);
 }
 
-template <typename TI>
-__device__ __forceinline__ const TI *ahat(const KArgs &A);
+template <typename TV>
+__device__ __forceinline__ const TV *ahat(const KArgs &A);
 template <>
 __device__ __forceinline__ const double *ahat<double>(const KArgs &A) { return A.a64; }
 template <>
 __device__ __forceinline__ const float *ahat<float>(const KArgs &A) { return A.a32; }
 
-// One row of an inner sweep (warp-cooperative): d = omega (g_r - (a_r, u)),
-// z_r += d, u += d a_r.  Matrix values are TV (FP64, or the FP32 copy in mixed
-// precision); u, z and all arithmetic are FP64, so the preconditioner is the
-// exact SSOR operator of the (rounded) matrix: linear and, for NE-SSOR, SPD.
-// Returns the row's z after the update (lane 0 only meaningful).
+// Row data of one sweep row held in registers: up to 32*RC column indices
+// and values per warp (RC per lane) and g_r.  Loads are issued one row ahead
+// of use (software pipelining), so their L2 latency overlaps the previous row
+// and the barrier.
 template <typename TV>
-__device__ __forceinline__ double sweep_row(int r, const int *__restrict__ rp, const int *__restrict__ ci,
-                                            const TV *__restrict__ a, double *u, double *z, double gr,
-                                            double om, bool first) {
+struct RowPre {
+  int r, k0, len;
+  int cv[RC];
+  TV av[RC];
+  double g;
+};
+
+// Per-warp sweep state in shared memory.  The rows of color c handled by warp
+// w are r0(c) + gw + j GW (j = 0, 1, ...); they own the slots
+// cum_w[c] + j of the warp's arrays: z (row corrections) and the row
+// descriptors (k0, len), built once per launch so no row pointer is read on
+// the critical path.
+struct ZStore {
+  double *zs;    // [KWPB][rw]
+  int2 *desc;    // [KWPB][rw]
+  int *cum;      // [KWPB][nc + 1]
+  int rw, nc;
+  __device__ __forceinline__ double *zw() const { return zs + (threadIdx.x >> 5) * rw; }
+  __device__ __forceinline__ const int2 *dw() const { return desc + (threadIdx.x >> 5) * rw; }
+  __device__ __forceinline__ const int *cw() const { return cum + (threadIdx.x >> 5) * (nc + 1); }
+};
+
+__device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int gw, int GW) {
+  // warp-parallel prefix sum of the per-color row counts of this warp
   const int lane = threadIdx.x & 31;
-  const int k0 = __ldg(rp + r), k1 = __ldg(rp + r + 1);
-  const int len = k1 - k0;
-  double s = 0.0;
-  if (len <= 32 * RC) {
-    int cv[RC];
-    double av[RC], uv[RC];
+  int *cw = Z.cum + (threadIdx.x >> 5) * (Z.nc + 1);
+  int2 *dw = Z.desc + (threadIdx.x >> 5) * Z.rw;
+  int carry = 0;
+  for (int base = 0; base < Z.nc; base += 32) {
+    const int c = base + lane;
+    int cnt = 0, r0 = 0;
+    if (c < Z.nc) {
+      r0 = __ldg(A.cptr + c);
+      const int rows = __ldg(A.cptr + c + 1) - r0;
+      cnt = rows > gw ? (rows - gw + GW - 1) / GW : 0;
+    }
+    int incl = cnt;
 #pragma unroll
-    for (int e = 0; e < RC; ++e) {
-      int k = k0 + lane + 32 * e;
-      if (k < k1) {
-        cv[e] = __ldg(ci + k);
-        av[e] = (double)__ldg(a + k);
-        uv[e] = ldcg(u + cv[e]);
-        s += av[e] * uv[e];
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (c < Z.nc) {
+      const int first = carry + incl - cnt;
+      cw[c] = first;
+      for (int j = 0; j < cnt; ++j) {
+        const int r = r0 + gw + j * GW;
+        const int k0 = __ldg(A.rp + r);
+        dw[first + j] = make_int2(k0, __ldg(A.rp + r + 1) - k0);
       }
     }
-    s = warp_sum(s);
-    const double d = om * (gr - s);
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) cw[Z.nc] = carry;
+  __syncwarp();
+}
+
+template <typename TV>
+__device__ __forceinline__ void row_fetch(const KArgs &A, const TV *__restrict__ a, const double *g, int r,
+                                          int2 kl, RowPre<TV> &P) {
+  const int lane = threadIdx.x & 31;
+  P.r = r;
+  P.k0 = kl.x;
+  P.len = kl.y;
+  if (P.len <= 32 * RC) {
 #pragma unroll
     for (int e = 0; e < RC; ++e) {
-      int k = k0 + lane + 32 * e;
-      if (k < k1) u[cv[e]] = uv[e] + d * av[e];
+      const int k = P.k0 + lane + 32 * e;
+      if (lane + 32 * e < P.len) {
+        P.cv[e] = __ldg(A.ci + k);
+        P.av[e] = __ldg(a + k);
+      }
     }
-    double zn = d;
-    if (lane == 0) {
-      zn = first ? d : ldcg(z + r) + d;
-      z[r] = zn;
-    }
-    return zn;
-  } else {
-    for (int k = k0 + lane; k < k1; k += 32) s += (double)__ldg(a + k) * ldcg(u + __ldg(ci + k));
-    s = warp_sum(s);
-    const double d = om * (gr - s);
-    for (int k = k0 + lane; k < k1; k += 32) {
-      int c = __ldg(ci + k);
-      u[c] = ldcg(u + c) + d * (double)__ldg(a + k);
-    }
-    double zn = d;
-    if (lane == 0) {
-      zn = first ? d : ldcg(z + r) + d;
-      z[r] = zn;
-    }
-    return zn;
   }
+  P.g = ldcg(g + r);
+}
+
+// One row of an inner sweep (warp-cooperative): d = omega (g_r - (a_r, u)),
+// u += d a_r; returns d (all lanes).  Matrix values are TV (FP64, or the FP32
+// copy in mixed precision); u and all arithmetic are FP64, so the
+// preconditioner is the exact SSOR operator of the (rounded) matrix: linear
+// and, for NE-SSOR, SPD.
+template <typename TV, typename GRP>
+__device__ __forceinline__ double row_update(const GRP &Gp, const KArgs &A, const TV *__restrict__ a,
+                                             const RowPre<TV> &P, double om) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (P.len <= 32 * RC) {
+    double uv[RC];
+#pragma unroll
+    for (int e = 0; e < RC; ++e)
+      if (lane + 32 * e < P.len) {
+        uv[e] = Gp.uld(P.cv[e]);
+        s += (double)P.av[e] * uv[e];
+      }
+    s = warp_sum(s);
+    const double d = om * (P.g - s);
+#pragma unroll
+    for (int e = 0; e < RC; ++e)
+      if (lane + 32 * e < P.len) Gp.ust(P.cv[e], uv[e] + d * (double)P.av[e]);
+    return d;
+  }
+  const int k1 = P.k0 + P.len;
+  for (int k = P.k0 + lane; k < k1; k += 32) s += (double)__ldg(a + k) * Gp.uld(__ldg(A.ci + k));
+  s = warp_sum(s);
+  const double d = om * (P.g - s);
+  for (int k = P.k0 + lane; k < k1; k += 32) {
+    const int c = __ldg(A.ci + k);
+    Gp.ust(c, Gp.uld(c) + d * (double)__ldg(a + k));
+  }
+  return d;
 }
 
 // A full application of the inner iterations on input g (m, double):
-// SSOR (2 passes per sweep) or SOR (1 pass).  u must be zero on entry.  If
-// acc != nullptr, each lane 0 adds z_r * g_r at the row's last visit.
-// Ends with a barrier after the last color.  Returns false on barrier failure.
-template <typename TV>
-__device__ bool inner_sweeps(const KArgs &A, GridBar &G, int *s_ok, const double *g, bool ssor,
-                             double *acc, Counters &C) {
+// SSOR (2 passes per sweep) or SOR (1 pass).  u must be zero on entry.  z
+// (row corrections) is kept in shared memory and written to A.z at the end.
+// If acc != nullptr, each lane 0 adds z_r * g_r at the row's last visit and
+// the barrier after the last color is left to the caller.  Returns false on
+// barrier failure.
+template <typename TV, typename GRP>
+__device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
+                             Counters &C, const ZStore &Z) {
   const TV *a = ahat<TV>(A);
-  double *u = (double *)A.u;
-  double *z = (double *)A.z;
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * KWPB + (threadIdx.x >> 5), GW = gridDim.x * KWPB;
+  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
   const double om = A.omega;
   const int passes = ssor ? 2 * A.ell : A.ell;
+  const int nc = A.nc;
+  const int nph = passes * nc;
+  double *zw = Z.zw();
+  const int2 *dw = Z.dw();
+  const int *cw = Z.cw();
   C.passes += passes;
-  for (int ps = 0; ps < passes; ++ps) {
-    const bool backward = ssor && (ps & 1);
-    const bool lastpass = ps == passes - 1;
-    for (int cc = 0; cc < A.nc; ++cc) {
-      const int c = backward ? A.nc - 1 - cc : cc;
-      const int r0 = __ldg(A.cptr + c), r1 = __ldg(A.cptr + c + 1);
-      for (int r = r0 + gw; r < r1; r += GW) {
-        const double gd = ldcg(g + r);
-        const double zn = sweep_row<TV>(r, A.rp, A.ci, a, u, z, gd, om, ps == 0);
-        if (lastpass && acc && lane == 0) *acc += zn * gd;
-      }
-      if (!(lastpass && cc == A.nc - 1 && acc)) {
-        if (!G.sync(s_ok)) return false;
-      }
+  // phase ph = (pass, color); backward passes reverse the color order
+  auto color_of = [&](int ph) {
+    const int ps = ph / nc, cc = ph - ps * nc;
+    return (ssor && (ps & 1)) ? nc - 1 - cc : cc;
+  };
+  // this warp's next row at or after (phase ph, index j within the phase):
+  // returns the phase holding it (nph if none) and sets *jj
+  auto next_row = [&](int ph, int j, int *jj) {
+    while (ph < nph) {
+      const int c = color_of(ph);
+      if (cw[c] + j < cw[c + 1]) { *jj = j; return ph; }
+      ++ph;
+      j = 0;
     }
+    return nph;
+  };
+  auto fetch = [&](int ph, int j, RowPre<TV> &P) {
+    const int c = color_of(ph);
+    const int r = __ldg(A.cptr + c) + gw + j * GW;
+    row_fetch<TV>(A, a, g, r, dw[cw[c] + j], P);
+  };
+  RowPre<TV> cur, nxt;
+  int jn = 0;
+  int phn = next_row(0, 0, &jn);  // phase of the row held in cur
+  if (phn < nph) fetch(phn, jn, cur);
+  int jcur = jn;
+  for (int ph = 0; ph < nph; ++ph) {
+    const int c = color_of(ph);
+    const int ps = ph / nc;
+    const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+    while (phn == ph) {
+      // issue the loads of the row after this one before working on this one
+      int j2 = 0;
+      const int ph2 = next_row(ph, jcur + 1, &j2);
+      if (ph2 < nph) fetch(ph2, j2, nxt);
+      const double d = row_update<TV>(Gp, A, a, cur, om);
+      if (lane == 0) {
+        const int slot = cw[c] + jcur;
+        const double zn = firstpass ? d : zw[slot] + d;
+        zw[slot] = zn;
+        if (lastpass && acc) *acc += zn * cur.g;
+      }
+      phn = ph2;
+      jcur = j2;
+      if (ph2 < nph) cur = nxt;
+    }
+    if (ph + 1 < nph || !acc) {
+      if (ph + 1 == nph) break;  // the final barrier comes after the z write-out
+      if (!Gp.sync(s_ok)) return false;
+    }
+  }
+  // z out to global memory (read by the vector phases after the next barrier)
+  __syncwarp();
+  for (int c = 0; c < nc; ++c) {
+    const int r0 = __ldg(A.cptr + c);
+    if (lane == 0)
+      for (int j = 0; cw[c] + j < cw[c + 1]; ++j) A.z[r0 + gw + j * GW] = zw[cw[c] + j];
+  }
+  if (!acc) {
+    if (!Gp.sync(s_ok)) return false;
   }
   return true;
 }
 
-// t = A_hat x in double, x gathered as xa[c] + beta * xb[c] (xb may be null)
-template <typename TU>
-__device__ __forceinline__ void spmv_rows(const KArgs &A, const TU *xa, double beta, const double *xb,
-                                          double *t, const double *sub /*t = sub - Ax if non-null*/) {
+// t = A_hat x in double (rows split over warps), x gathered as x(c) (a
+// callable); t = sub - A_hat x when sub is non-null
+template <typename GRP, typename XF>
+__device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, double *t, const double *sub) {
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * KWPB + (threadIdx.x >> 5), GW = gridDim.x * KWPB;
+  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
   for (int r = gw; r < A.m; r += GW) {
     const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
     double s = 0.0;
-    for (int k = k0 + lane; k < k1; k += 32) {
-      const int c = __ldg(A.ci + k);
-      double xv = (double)ldcg(xa + c);
-      if (xb) xv += beta * ldcg(xb + c);
-      s += __ldg(A.a64 + k) * xv;
-    }
+    for (int k = k0 + lane; k < k1; k += 32) s += __ldg(A.a64 + k) * x(__ldg(A.ci + k));
     s = warp_sum(s);
     if (lane == 0) t[r] = sub ? ldcg(sub + r) - s : s;
   }
 }
 
 // out = A_hat^T x in double through the CSC (warp per column); returns this
-// thread's share of ||out||^2
-template <typename TX>
-__device__ __forceinline__ double csc_products(const KArgs &A, const TX *x, double *out) {
+// thread's share of ||out||^2 and, if old != nullptr, of (old, out) where old
+// is read before out is written (old may alias out)
+template <typename GRP>
+__device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, const double *x, double *out,
+                                               double *dot_old = nullptr) {
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * KWPB + (threadIdx.x >> 5), GW = gridDim.x * KWPB;
+  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
   double acc = 0.0;
   for (int j = gw; j < A.n; j += GW) {
     const int q0 = __ldg(A.cp + j), q1 = __ldg(A.cp + j + 1);
     double s = 0.0;
-    for (int q = q0 + lane; q < q1; q += 32) s += __ldg(A.aht + q) * (double)ldcg(x + __ldg(A.ri + q));
+    for (int q = q0 + lane; q < q1; q += 32) s += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
     s = warp_sum(s);
     if (lane == 0) {
+      if (dot_old) *dot_old += ldcg(out + j) * s;
       out[j] = s;
       acc += s * s;
     }
@@ -282,41 +476,48 @@ __device__ __forceinline__ double csc_products(const KArgs &A, const TX *x, doub
   return acc;
 }
 
-// Sweep state accessors (u, z are FP64 in both precisions; f32 selects the
-// FP32 copy of the matrix values inside the sweeps).
-struct Inner {
-  void *u, *z;
-  bool f32;
-  __device__ __forceinline__ double zget(int i) const { return ldcg((const double *)z + i); }
-  __device__ __forceinline__ double uget(int j) const { return ldcg((const double *)u + j); }
-};
-
-__device__ __forceinline__ double csc_z(const KArgs &A, const Inner &I, double *out) {
-  return csc_products<double>(A, (const double *)I.z, out);
+template <typename GRP>
+__device__ __forceinline__ GRP make_group(const KArgs &A);
+template <>
+__device__ __forceinline__ GridGrp make_group<GridGrp>(const KArgs &A) {
+  return GridGrp{&A.ctl->bar, &A.ctl->status, 0ull, A.u};
+}
+template <>
+__device__ __forceinline__ ClusterGrp make_group<ClusterGrp>(const KArgs &A) {
+  extern __shared__ double dyn_smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  return ClusterGrp{dyn_smem, (unsigned)A.u_shift, (1u << A.u_shift) - 1u, cl.block_rank(), cl.num_blocks(), 0};
 }
 
-template <int METH, typename TV>
+template <int METH, typename TV, typename GRP>
 __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
   __shared__ double sred[8 * KWPB];
   __shared__ int s_ok;
-  GridBar G{&A.ctl->bar, &A.ctl->status, 0ull, gridDim.x};
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, NT = gridDim.x * blockDim.x;
+  GRP Gp = make_group<GRP>(A);
+  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
+  const bool cta0 = Gp.rank() == 0 && threadIdx.x == 0;
   const int m = A.m, n = A.n;
-  Inner I{A.u, A.z, A.f32 != 0};
   Counters Cn;
-  double *ud = (double *)A.u;  // zeroing as doubles clears either representation
+  extern __shared__ double dyn_smem[];
+  char *zbase = (char *)dyn_smem + A.z_off;
+  ZStore Z{(double *)zbase, (int2 *)(zbase + sizeof(double) * KWPB * A.rw),
+           (int *)(zbase + (sizeof(double) + sizeof(int2)) * KWPB * A.rw), A.rw, A.nc};
+  zstore_init(A, Z, Gp.rank() * KWPB + (threadIdx.x >> 5), Gp.size() * KWPB);
+  auto uget = [&](int j) { return Gp.uld(j); };
+  auto zget = [&](int i) { return ldcg(A.z + i); };
 
   // ---- sweep-only mode (lpk_sweep) ----------------------------------------
   if (METH == M_SWEEP) {
-    for (int j = tid; j < n; j += NT) ud[j] = 0.0;
-    if (!G.sync(&s_ok)) return;
-    if (!inner_sweeps<TV>(A, G, &s_ok, A.f, A.method == M_SWEEP_SSOR, nullptr, Cn)) return;
-    for (int j = tid; j < n; j += NT) A.out_u[j] = I.uget(j);
-    for (int i = tid; i < m; i += NT) A.out_z[i] = I.zget(i);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Gp.uzero(n);
+    if (!Gp.sync(&s_ok)) return;
+    if (!inner_sweeps<TV>(A, Gp, &s_ok, A.f, A.method == M_SWEEP_SSOR, nullptr, Cn, Z)) return;
+    for (int j = tid; j < n; j += NT) A.out_u[j] = uget(j);
+    for (int i = tid; i < m; i += NT) A.out_z[i] = zget(i);
+    if (cta0) {
       A.ctl->passes = Cn.passes;
-      A.ctl->barriers = (long long)G.epoch;
+      A.ctl->barriers = Gp.barriers();
     }
+    Gp.sync(&s_ok);  // no CTA of a cluster may exit while peers read its shared memory
     return;
   }
 
@@ -330,83 +531,85 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       A.dy[i] = 0.0;
       v[0] += fi * fi;
     }
-    for (int j = tid; j < n; j += NT) {
-      A.dw[j] = 0.0;
-      ud[j] = 0.0;
-    }
+    for (int j = tid; j < n; j += NT) A.dw[j] = 0.0;
+    Gp.uzero(n);
     if (METH == M_CGNE) {  // the starting iterate is the best one so far
       for (int j = tid; j < n; j += NT) A.bw[j] = 0.0;
       for (int i = tid; i < m; i += NT) A.by[i] = 0.0;
     }
-    put_partials<1>(v, A.part, sred);
-    if (!G.sync(&s_ok)) return;
-    get_sums<1>(v, A.part, sred);
+    put_partials<1>(Gp, v, A.part, sred);
+    if (!Gp.sync(&s_ok)) return;
+    get_sums<1>(Gp, v, A.part, sred);
     res0 = sqrt(v[0]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (cta0) {
       A.ctl->res0 = res0;
       if (A.hist) A.hist[0] = res0;
     }
     if (res0 == 0.0) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) { A.ctl->converged = 1; A.ctl->res = 0.0; }
+      if (cta0) { A.ctl->converged = 1; A.ctl->res = 0.0; }
       return;
     }
   }
   const double target = A.tol * res0;  // identical in every CTA
-  int k = 0, k32 = 0, restarts = 0, escal = 0, reason = EXIT_MAXIT;
+  int k = 0, restarts = 0, reason = EXIT_MAXIT;
   double gnorm = res0;
   double *p_cur = A.p0, *p_nxt = A.p1;
-  const bool flex = false;  // fixed linear preconditioner in both precisions: the paper's beta
 
   for (;;) {  // restart loop
     double gamma = 0.0, beta = 0.0;
     bool first = true;
     reason = EXIT_MAXIT;
     double best = gnorm;
-    int best_k = k;
     if (METH == M_MRNE) {
       // q0 = A^T C g0 (w-space), qt0 = C g0
-      if (!inner_sweeps<TV>(A, G, &s_ok, A.g, true, nullptr, Cn)) return;
+      if (!inner_sweeps<TV>(A, Gp, &s_ok, A.g, true, nullptr, Cn, Z)) return;
       double v[1] = {0.0};
       if (A.wy) {
         ++Cn.cols;
-        v[0] = csc_z(A, I, A.q);  // q0 = A_hat^T z in FP64
+        v[0] = csc_products(Gp, A, A.z, A.q);  // q0 = A_hat^T z in FP64
       } else {
         for (int j = tid; j < n; j += NT) {
-          double qj = I.uget(j);
+          double qj = uget(j);
           A.q[j] = qj;
           v[0] += qj * qj;
         }
       }
-      for (int i = tid; i < m; i += NT) A.qt[i] = I.zget(i);
-      put_partials<1>(v, A.part, sred);
-      if (!G.sync(&s_ok)) return;
-      get_sums<1>(v, A.part, sred);
+      for (int i = tid; i < m; i += NT) A.qt[i] = zget(i);
+      put_partials<1>(Gp, v, A.part, sred);
+      if (!Gp.sync(&s_ok)) return;
+      get_sums<1>(Gp, v, A.part, sred);
       gamma = v[0];
       while (true) {
         if (gnorm <= target) { reason = EXIT_CONV; break; }
         if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
-        if (I.f32 && k - best_k >= A.stall) { reason = EXIT_STALL; break; }
         // P1: p = q + beta p_old (fused), pt = qt + beta pt, t = A_hat p, u = 0
         for (int j = tid; j < n; j += NT) {
           double qj = ldcg(A.q + j);
           p_nxt[j] = first ? qj : qj + beta * ldcg(p_cur + j);
-          ud[j] = 0.0;
         }
+        Gp.uzero(n);
         for (int i = tid; i < m; i += NT) {
           double qi = ldcg(A.qt + i);
           A.pt[i] = first ? qi : qi + beta * ldcg(A.pt + i);
         }
         ++Cn.rows;
-        spmv_rows<double>(A, A.q, first ? 0.0 : beta, first ? nullptr : p_cur, A.t, nullptr);
+        {
+          const double *qv = A.q, *pv = p_cur;
+          const double bb = beta;
+          if (first)
+            spmv_rows(Gp, A, [&](int c) { return ldcg(qv + c); }, A.t, nullptr);
+          else
+            spmv_rows(Gp, A, [&](int c) { return ldcg(qv + c) + bb * ldcg(pv + c); }, A.t, nullptr);
+        }
         { double *tmp = p_cur; p_cur = p_nxt; p_nxt = tmp; }
         first = false;
-        if (!G.sync(&s_ok)) return;
+        if (!Gp.sync(&s_ok)) return;
         // P2: [vt, v] = SSOR(t), (v, p) = (vt, t)
         double acc[1] = {0.0};
-        if (!inner_sweeps<TV>(A, G, &s_ok, A.t, true, &acc[0], Cn)) return;
-        put_partials<1>(acc, A.part, sred);
-        if (!G.sync(&s_ok)) return;
-        get_sums<1>(acc, A.part, sred);
+        if (!inner_sweeps<TV>(A, Gp, &s_ok, A.t, true, &acc[0], Cn, Z)) return;
+        put_partials<1>(Gp, acc, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<1>(Gp, acc, A.part, sred);
         const double vp = acc[0];
         if (!(vp > 0.0) || !(gamma > 0.0) || !isfinite(vp)) { reason = EXIT_BREAK; break; }
         const double alpha = gamma / vp;
@@ -416,7 +619,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           double pj = ldcg(p_cur + j);
           A.dw[j] = ldcg(A.dw + j) + alpha * pj;
           if (!A.wy) {
-            double qj = ldcg(A.q + j) - alpha * I.uget(j);
+            double qj = ldcg(A.q + j) - alpha * uget(j);
             A.q[j] = qj;
             w[0] += qj * qj;
           }
@@ -425,73 +628,54 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           A.dy[i] = ldcg(A.dy + i) + alpha * ldcg(A.pt + i);
           double gi = ldcg(A.g + i) - alpha * ldcg(A.t + i);
           A.g[i] = gi;
-          A.qt[i] = ldcg(A.qt + i) - alpha * I.zget(i);
+          A.qt[i] = ldcg(A.qt + i) - alpha * zget(i);
           w[1] += gi * gi;
         }
-        put_partials<2>(w, A.part, sred);
-        if (!G.sync(&s_ok)) return;
-        get_sums<2>(w, A.part, sred);
+        put_partials<2>(Gp, w, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<2>(Gp, w, A.part, sred);
         double gnew = w[0];
-        if (A.wy) {  // P4: q = A_hat^T qt in FP64; gamma' = ||q||^2 and (q_old, q)
-          const int lane = threadIdx.x & 31;
-          const int gw = blockIdx.x * KWPB + (threadIdx.x >> 5), GW = gridDim.x * KWPB;
-          double w2[2] = {0.0, 0.0};
+        if (A.wy) {  // P4: q = A_hat^T qt in FP64, gamma' = ||q||^2
           ++Cn.cols;
-          for (int j = gw; j < n; j += GW) {
-            const int q0 = __ldg(A.cp + j), q1 = __ldg(A.cp + j + 1);
-            double sacc = 0.0;
-            for (int q = q0 + lane; q < q1; q += 32) sacc += __ldg(A.aht + q) * ldcg(A.qt + __ldg(A.ri + q));
-            sacc = warp_sum(sacc);
-            if (lane == 0) {
-              const double qo = ldcg(A.q + j);
-              A.q[j] = sacc;
-              w2[0] += sacc * sacc;
-              w2[1] += qo * sacc;
-            }
-          }
-          put_partials<2>(w2, A.part, sred);
-          if (!G.sync(&s_ok)) return;
-          get_sums<2>(w2, A.part, sred);
+          double w2[1] = {csc_products(Gp, A, A.qt, A.q)};
+          put_partials<1>(Gp, w2, A.part, sred);
+          if (!Gp.sync(&s_ok)) return;
+          get_sums<1>(Gp, w2, A.part, sred);
           gnew = w2[0];
-          beta = flex ? (w2[0] - w2[1]) / gamma : w2[0] / gamma;
-        } else {
-          beta = gnew / gamma;
         }
+        beta = gnew / gamma;
         gamma = gnew;
         ++k;
-        if (I.f32) ++k32;
         gnorm = sqrt(w[1]);
-        if (A.hist && blockIdx.x == 0 && threadIdx.x == 0) A.hist[k] = gnorm;
-        if (gnorm < best) { best = gnorm; best_k = k; }
+        if (A.hist && cta0) A.hist[k] = gnorm;
       }
     } else {  // CGNE
       // z0 = C g0, u0 = A^T z0, gamma0 = (g0, z0)
       double acc[1] = {0.0};
-      if (!inner_sweeps<TV>(A, G, &s_ok, A.g, true, &acc[0], Cn)) return;
-      put_partials<1>(acc, A.part, sred);
-      if (!G.sync(&s_ok)) return;
-      get_sums<1>(acc, A.part, sred);
+      if (!inner_sweeps<TV>(A, Gp, &s_ok, A.g, true, &acc[0], Cn, Z)) return;
+      put_partials<1>(Gp, acc, A.part, sred);
+      if (!Gp.sync(&s_ok)) return;
+      get_sums<1>(Gp, acc, A.part, sred);
       gamma = acc[0];
       if (A.wy) {  // u0 = A_hat^T z0 in FP64
         ++Cn.cols;
-        csc_z(A, I, A.uw);
-        if (!G.sync(&s_ok)) return;
+        csc_products(Gp, A, A.z, A.uw);
+        if (!Gp.sync(&s_ok)) return;
       }
       bool save_best = false;
       while (true) {
         if (gnorm <= target) { reason = EXIT_CONV; break; }
         if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
-        if (I.f32 && k - best_k >= A.stall) { reason = EXIT_STALL; break; }
         // P1: q = u + beta q_old, qt = z + beta qt, t = A_hat q, (q, q)
         double v[1] = {0.0};
         for (int j = tid; j < n; j += NT) {
-          double uj = A.wy ? ldcg(A.uw + j) : I.uget(j);
+          double uj = A.wy ? ldcg(A.uw + j) : uget(j);
           double qj = first ? uj : uj + beta * ldcg(A.q + j);
           p_nxt[j] = qj;
           v[0] += qj * qj;
         }
         for (int i = tid; i < m; i += NT) {
-          double zi = I.zget(i);
+          double zi = zget(i);
           A.qt[i] = first ? zi : zi + beta * ldcg(A.qt + i);
         }
         if (save_best) {  // keep the minimum-residual iterate (Sec. 4.2)
@@ -499,99 +683,98 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           for (int i = tid; i < m; i += NT) A.by[i] = ldcg(A.dy + i);
         }
         ++Cn.rows;
-        if (A.wy)
-          spmv_rows<double>(A, A.uw, first ? 0.0 : beta, first ? nullptr : A.q, A.t, nullptr);
-        else
-          spmv_rows<double>(A, (const double *)A.u, first ? 0.0 : beta, first ? nullptr : A.q, A.t, nullptr);
-        put_partials<1>(v, A.part, sred);
+        {
+          const double *qv = A.q, *uwv = A.uw;
+          const double bb = beta;
+          const bool fst = first, wy = A.wy != 0;
+          spmv_rows(Gp, A,
+                    [&](int c) {
+                      double uj = wy ? ldcg(uwv + c) : Gp.uld(c);
+                      return fst ? uj : uj + bb * ldcg(qv + c);
+                    },
+                    A.t, nullptr);
+        }
+        put_partials<1>(Gp, v, A.part, sred);
         first = false;
-        if (!G.sync(&s_ok)) return;
-        get_sums<1>(v, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<1>(Gp, v, A.part, sred);
         const double qq = v[0];
         if (!(qq > 0.0) || !(gamma > 0.0) || !isfinite(gamma)) { reason = EXIT_BREAK; break; }
         const double alpha = gamma / qq;
-        // P2: dw += alpha q, dy += alpha qt, g -= alpha t, u = 0, ||g||, (g, z_old)
-        double w[2] = {0.0, 0.0};
+        // P2: dw += alpha q, dy += alpha qt, g -= alpha t, u = 0, ||g||
+        double w[1] = {0.0};
         for (int j = tid; j < n; j += NT) {
           double qj = ldcg(p_nxt + j);
           A.q[j] = qj;
           A.dw[j] = ldcg(A.dw + j) + alpha * qj;
-          ud[j] = 0.0;
         }
+        Gp.uzero(n);
         for (int i = tid; i < m; i += NT) {
           A.dy[i] = ldcg(A.dy + i) + alpha * ldcg(A.qt + i);
           double gi = ldcg(A.g + i) - alpha * ldcg(A.t + i);
           A.g[i] = gi;
           w[0] += gi * gi;
-          if (flex) w[1] += gi * I.zget(i);
         }
-        put_partials<2>(w, A.part, sred);
-        if (!G.sync(&s_ok)) return;
-        get_sums<2>(w, A.part, sred);
+        put_partials<1>(Gp, w, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<1>(Gp, w, A.part, sred);
         ++k;
-        if (I.f32) ++k32;
         gnorm = sqrt(w[0]);
-        if (A.hist && blockIdx.x == 0 && threadIdx.x == 0) A.hist[k] = gnorm;
+        if (A.hist && cta0) A.hist[k] = gnorm;
         save_best = gnorm < best;
-        if (save_best) { best = gnorm; best_k = k; }
+        if (save_best) best = gnorm;
         if (gnorm <= target) { reason = EXIT_CONV; break; }
         if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
         // P3: [z, u] = SSOR(g), gamma' = (g, z)
         double a2[1] = {0.0};
-        if (!inner_sweeps<TV>(A, G, &s_ok, A.g, true, &a2[0], Cn)) return;
-        put_partials<1>(a2, A.part, sred);
-        if (!G.sync(&s_ok)) return;
-        get_sums<1>(a2, A.part, sred);
-        beta = flex ? (a2[0] - w[1]) / gamma : a2[0] / gamma;
+        if (!inner_sweeps<TV>(A, Gp, &s_ok, A.g, true, &a2[0], Cn, Z)) return;
+        put_partials<1>(Gp, a2, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<1>(Gp, a2, A.part, sred);
+        beta = a2[0] / gamma;
         gamma = a2[0];
         if (A.wy) {
           ++Cn.cols;
-          csc_z(A, I, A.uw);
-          if (!G.sync(&s_ok)) return;
+          csc_products(Gp, A, A.z, A.uw);
+          if (!Gp.sync(&s_ok)) return;
         }
       }
       if (reason != EXIT_CONV && best < gnorm) {
         // bw/by hold the minimum-residual iterate (the current one is worse)
         for (int j = tid; j < n; j += NT) A.dw[j] = ldcg(A.bw + j);
         for (int i = tid; i < m; i += NT) A.dy[i] = ldcg(A.by + i);
-        if (!G.sync(&s_ok)) return;
+        if (!Gp.sync(&s_ok)) return;
       }
     }
     // ---- explicit residual g = f - A_hat dw; restart when it disagrees ------
     if (A.wy) {  // dw = A_hat^T dy in FP64 keeps the two spaces consistent
       ++Cn.cols;
-      csc_products<double>(A, A.dy, A.dw);
-      if (!G.sync(&s_ok)) return;
+      csc_products(Gp, A, A.dy, A.dw);
+      if (!Gp.sync(&s_ok)) return;
     }
     double v[1] = {0.0};
     ++Cn.rows;
-    spmv_rows<double>(A, A.dw, 0.0, nullptr, A.g, A.f);
-    for (int j = tid; j < n; j += NT) ud[j] = 0.0;
-    if (!G.sync(&s_ok)) return;
+    {
+      const double *dwv = A.dw;
+      spmv_rows(Gp, A, [&](int c) { return ldcg(dwv + c); }, A.g, A.f);
+    }
+    Gp.uzero(n);
+    if (!Gp.sync(&s_ok)) return;
     for (int i = tid; i < m; i += NT) {
       double gi = ldcg(A.g + i);
       v[0] += gi * gi;
     }
-    put_partials<1>(v, A.part, sred);
-    if (!G.sync(&s_ok)) return;
-    get_sums<1>(v, A.part, sred);
+    put_partials<1>(Gp, v, A.part, sred);
+    if (!Gp.sync(&s_ok)) return;
+    get_sums<1>(Gp, v, A.part, sred);
     const double res = sqrt(v[0]);
     gnorm = res;
     if (METH == M_CGNE) {  // a restart starts from the current iterate
       for (int j = tid; j < n; j += NT) A.bw[j] = ldcg(A.dw + j);
       for (int i = tid; i < m; i += NT) A.by[i] = ldcg(A.dy + i);
     }
-    // mixed precision: a stalled FP32 phase, or an FP32 recurrence the explicit
-    // residual does not confirm, continues with FP64 inner sweeps
-    const bool escalate = res > target && I.f32 && k < A.maxit &&
-                          (reason == EXIT_STALL || reason == EXIT_CONV);
-    if (escalate) {
-      I.f32 = false;
-      ++escal;
-      continue;
-    }
     if (res <= target || reason != EXIT_CONV || restarts >= A.max_restarts || k >= A.maxit) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (cta0) {
         A.ctl->res = res;
         A.ctl->converged = res <= target;
         A.ctl->breakdown = reason == EXIT_BREAK;
@@ -600,21 +783,19 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
     }
     ++restarts;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (cta0) {
     A.ctl->passes = Cn.passes;
     A.ctl->rows = Cn.rows;
     A.ctl->cols = Cn.cols;
-    A.ctl->barriers = (long long)G.epoch;
+    A.ctl->barriers = Gp.barriers();
     A.ctl->iters = k;
-    A.ctl->iters32 = k32;
     A.ctl->restarts = restarts;
-    A.ctl->escalations = escal;
   }
+  Gp.sync(&s_ok);  // no CTA of a cluster may exit while peers read its shared memory
 }
 
 struct Workspace {
-  double *g, *t, *qt, *pt, *by, *q, *p0, *p1, *bw, *dwtmp;
-  void *u, *z;
+  double *g, *t, *qt, *pt, *by, *q, *p0, *p1, *bw, *uw, *u, *z;
 };
 
 lpk_status get_ws(lpk_ctx *ctx, DevProblem &P, Workspace &W) {
@@ -639,7 +820,7 @@ lpk_status get_ws(lpk_ctx *ctx, DevProblem &P, Workspace &W) {
   W.p1 = b; b += n;
   W.bw = b; b += n;
   W.u = b; b += n;
-  W.dwtmp = b; b += n;
+  W.uw = b; b += n;
   return LPK_OK;
 }
 
@@ -651,33 +832,126 @@ lpk_status ensure_kctl(lpk_ctx *ctx) {
   return LPK_OK;
 }
 
+template <typename GRP>
 void *kernel_for(int method, int f32) {
-  if (method == M_MRNE) return f32 ? (void *)k_krylov<M_MRNE, float> : (void *)k_krylov<M_MRNE, double>;
-  if (method == M_CGNE) return f32 ? (void *)k_krylov<M_CGNE, float> : (void *)k_krylov<M_CGNE, double>;
-  return f32 ? (void *)k_krylov<M_SWEEP, float> : (void *)k_krylov<M_SWEEP, double>;
+  if (method == M_MRNE) return f32 ? (void *)k_krylov<M_MRNE, float, GRP> : (void *)k_krylov<M_MRNE, double, GRP>;
+  if (method == M_CGNE) return f32 ? (void *)k_krylov<M_CGNE, float, GRP> : (void *)k_krylov<M_CGNE, double, GRP>;
+  return f32 ? (void *)k_krylov<M_SWEEP, float, GRP> : (void *)k_krylov<M_SWEEP, double, GRP>;
 }
 
-lpk_status launch(lpk_ctx *ctx, KArgs &A, int slot) {
-  void *fn = kernel_for(A.method, A.f32);
-  if (ctx->kgrid_cache[slot] == 0) {
-    int per_sm = 0;
-    LPK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KTPB, 0));
-    if (per_sm < 1) {
-      ctx->err = "persistent Krylov kernel does not fit on an SM";
-      return LPK_CUDA_ERROR;
-    }
-    ctx->kgrid_cache[slot] = ctx->num_sms;  // one CTA per SM keeps the barrier cheap
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+// shared memory of the per-warp z slots and color offsets for GW warps
+size_t zstore_bytes(const DevProblem &P, int GW, int *rw) {
+  *rw = (P.m + GW - 1) / GW + P.n_colors;
+  return (sizeof(double) + sizeof(int2)) * KWPB * (size_t)*rw + sizeof(int) * KWPB * (size_t)(P.n_colors + 1);
+}
+
+// Cluster size and u slice (2^shift doubles per CTA) for a problem, or 0 when
+// the grid path is used.  The cluster path keeps u (n doubles) in the CTAs'
+// shared memory.
+int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int *shift) {
+  if (ctx->cluster_mode == 1 || P.n <= 0) return 0;  // forced grid
+  int cs = 2;
+  while (cs < MAX_CLUSTER && (long long)cs * 16384 < P.nnz) cs *= 2;
+  if (ctx->cluster_size_override > 0) cs = ctx->cluster_size_override;
+  int s = 5;
+  while ((1ll << s) * cs < P.n) ++s;
+  if (s > MAX_SHIFT) {
+    if (ctx->cluster_mode == 2) return -1;  // forced cluster impossible
+    return 0;
   }
-  dim3 grid(ctx->kgrid_cache[slot]), block(KTPB);
-  void *args[] = {&A};
+  *shift = s;
+  return cs;
+}
+
+lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   if (!ctx->ev0) {
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
   }
+  int shift = 0;
+  const int cs = cluster_plan(ctx, P, &shift);
+  if (cs < 0) {
+    ctx->err = "cluster path requested but u does not fit in one cluster's shared memory";
+    return LPK_INVALID_ARG;
+  }
+  int use_cs = cs;
+  void *cfn = nullptr;
+  size_t smem = 0;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  if (cs > 0) {
+    // the cluster must be co-schedulable and fit in shared memory; otherwise
+    // use a smaller one (u per CTA doubles) or the grid path
+    cfn = kernel_for<ClusterGrp>(A.method, f32);
+    for (use_cs = cs; use_cs >= 2; use_cs /= 2) {
+      int s2 = shift;
+      while ((1ll << s2) * use_cs < P.n) ++s2;
+      if (s2 > MAX_SHIFT) { use_cs = 0; break; }
+      int rw = 0;
+      const size_t zb = zstore_bytes(P, use_cs * KWPB, &rw);
+      smem = (sizeof(double) << s2) + zb;
+      if (smem > SMEM_LIMIT) continue;
+      LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeNonPortableClusterSizeAllowed, use_cs > 8 ? 1 : 0));
+      cfg.gridDim = dim3(use_cs);
+      cfg.blockDim = dim3(KTPB);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = ctx->stream;
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = use_cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, cfn, &cfg) == cudaSuccess && nclusters > 0) {
+        shift = s2;
+        A.u_shift = s2;
+        A.rw = rw;
+        A.z_off = (int)(sizeof(double) << s2);
+        break;
+      }
+      cudaGetLastError();
+    }
+    if (use_cs < 2) use_cs = 0;
+    if (use_cs == 0 && ctx->cluster_mode == 2) {
+      ctx->err = "no cluster configuration of the persistent kernel can be scheduled";
+      return LPK_CUDA_ERROR;
+    }
+  }
+  void *gfn = nullptr;
+  size_t gsmem = 0;
+  if (use_cs == 0) {
+    gfn = kernel_for<GridGrp>(A.method, f32);
+    int rw = 0;
+    gsmem = zstore_bytes(P, ctx->num_sms * KWPB, &rw);
+    if (gsmem > SMEM_LIMIT) {
+      ctx->err = "too many colors for the shared-memory sweep state";
+      return LPK_INVALID_ARG;
+    }
+    LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    int per_sm = 0;
+    LPK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfn, KTPB, gsmem));
+    if (per_sm < 1) {
+      ctx->err = "persistent Krylov kernel does not fit on an SM";
+      return LPK_CUDA_ERROR;
+    }
+    A.rw = rw;
+    A.z_off = 0;
+    A.u_shift = 0;
+  }
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->kctl, 0, sizeof(KrylovCtl), ctx->stream));
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   LPK_COUNT(ctx);
-  LPK_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(fn, grid, block, args, 0, ctx->stream));
+  void *args[] = {&A};
+  if (use_cs > 0) {
+    LPK_CUDA_TRY(ctx, cudaLaunchKernelExC(&cfg, cfn, args));
+  } else {
+    // one CTA per SM keeps the grid barrier cheap
+    LPK_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(gfn, dim3(ctx->num_sms), dim3(KTPB), args, gsmem, ctx->stream));
+  }
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_kctl, ctx->kctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, ctx->stream));
   LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -691,6 +965,7 @@ lpk_status launch(lpk_ctx *ctx, KArgs &A, int slot) {
   ctx->stats.row_passes += h->rows;
   ctx->stats.csc_passes += h->cols;
   ctx->stats.barriers += h->barriers;
+  ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
     ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out";
     return LPK_TIMEOUT;
@@ -711,7 +986,7 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.cp = P.cp;
   A.ri = P.ri;
   A.aht = P.aht;
-  A.uw = W.dwtmp;
+  A.uw = W.uw;
   A.ell = ell;
   A.omega = omega;
   A.g = W.g; A.t = W.t; A.qt = W.qt; A.pt = W.pt; A.by = W.by;
@@ -740,20 +1015,15 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   A.tol = tol;
   A.maxit = maxit;
   A.method = method == LPK_MRNE ? M_MRNE : M_CGNE;
-  // FP64: one cycle (plus up to 3 restarts when the explicit residual does not
-  // confirm the recurrence); mixed: cycles of 1e-4 reduction each
   // FP64: the paper's recurrences; up to 3 restarts when the explicit residual
   // does not confirm the recurrence.  Mixed: sweeps over the FP32 copy of the
   // scaled matrix with FP64 accumulation, w-space images by FP64 CSC products.
-  A.cycle_tol = 0.0;
   A.wy = precision == LPK_MIXED ? 1 : 0;
-  A.f32 = precision == LPK_MIXED ? 1 : 0;
-  A.stall = 1 << 30;  // no escalation: the FP32-valued preconditioner is a fixed SPD operator
   A.max_restarts = 3;
   A.dw = dw;
   A.dy = dy_hat;
   A.hist = hist;
-  st = launch(ctx, A, 0);
+  st = launch(ctx, P, A, precision == LPK_MIXED);
   if (st != LPK_OK) return st;
   const KrylovCtl *h = (const KrylovCtl *)ctx->h_kctl;
   out->iters = h->iters;
@@ -762,8 +1032,8 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   out->breakdown = h->breakdown;
   out->res0 = h->res0;
   out->res = h->res;
-  out->iters32 = h->iters32;
-  out->escalations = h->escalations;
+  out->iters32 = precision == LPK_MIXED ? h->iters : 0;
+  out->escalations = 0;
   return LPK_OK;
 }
 
@@ -779,6 +1049,5 @@ lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int 
   // NE-SOR keeps the w-space iterate in u (n) and the row corrections in z (m)
   A.out_z = z;
   A.out_u = u;
-  A.f32 = precision == LPK_MIXED ? 1 : 0;
-  return launch(ctx, A, 0);
+  return launch(ctx, P, A, precision == LPK_MIXED);
 }

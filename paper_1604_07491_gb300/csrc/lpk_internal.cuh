@@ -81,6 +81,11 @@ struct lpk_ctx {
   double *h_red = nullptr;       // pinned host copy of red_out
   int red_blocks = 0;
 
+  // execution path of the persistent Krylov kernel (lpk_set_exec)
+  int cluster_mode = 0;          // 0 auto, 1 grid, 2 cluster
+  int cluster_size_override = 0; // 0: chosen from nnz
+  int last_cluster = 0;          // cluster size of the last launch (0: grid)
+
   // problems prepared on this context (freed with it)
   std::vector<lpk_problem *> problems;
 

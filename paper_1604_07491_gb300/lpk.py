@@ -21,12 +21,13 @@ STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREA
           6: "EMPTY_ROW_INCONSISTENT", 7: "EMPTY_COL_UNBOUNDED", 8: "INVALID_ARG", 9: "OOM",
           10: "CUDA_ERROR"}
 MRNE, CGNE, ABGMRES = 0, 1, 2
+EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER = 0, 1, 2
 FP64, MIXED = 0, 1
 NE_SSOR, NE_SOR = 0, 1
 
 # every symbol include/lpk.h declares
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
-           "lpk_reset_stats", "lpk_prepare",
+           "lpk_reset_stats", "lpk_set_exec", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
            "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_lp_solve"]
 
@@ -75,7 +76,8 @@ class KrylovInfo(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("krylov_launches", C.c_int64), ("krylov_ms", C.c_double),
                 ("krylov_iters", C.c_int64), ("sweep_passes", C.c_int64), ("row_passes", C.c_int64),
-                ("csc_passes", C.c_int64), ("barriers", C.c_int64)]
+                ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +102,7 @@ def load():
         "lpk_default_options": (None, [C.POINTER(Options)]),
         "lpk_get_stats": (I32, [P, C.POINTER(Stats)]),
         "lpk_reset_stats": (I32, [P]),
+        "lpk_set_exec": (I32, [P, I32, I32]),
         "lpk_prepare": (I32, [P, C.POINTER(Matrix), C.c_uint64, C.POINTER(P)]),
         "lpk_problem_free": (None, [P]),
         "lpk_problem_dims": (I32, [P, P, P, P, P]),
@@ -199,6 +202,10 @@ class Context:
 
     def reset_stats(self):
         load().lpk_reset_stats(self._h)
+
+    def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
+        """Krylov kernel path: EXEC_AUTO, EXEC_GRID or EXEC_CLUSTER (size 0/2/4/8/16)."""
+        _check(self._h, load().lpk_set_exec(self._h, exec_mode, cluster_size))
 
 
 def default_options(**kw) -> Options:

@@ -37,6 +37,23 @@ def ctx(lpk):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_grid(lpk):
+    """A context forced onto the grid path (software grid barrier, u in HBM)."""
+    c = lpk.Context(0)
+    c.set_exec(lpk.EXEC_GRID)
+    yield c
+    c.close()
+
+
+@pytest.fixture(params=["auto", "grid"])
+def pctx(request, ctx, ctx_grid):
+    """Both execution paths of the persistent kernel: auto picks the cluster
+    path (hardware cluster barrier, u in distributed shared memory) for every
+    size used here."""
+    return ctx if request.param == "auto" else ctx_grid
+
+
 def certs(lp, x, y, s):
     A = lp.scipy()
     pinf = np.linalg.norm(lp.b - A @ x) / max(np.linalg.norm(lp.b), 1)
@@ -108,9 +125,9 @@ def rel(a, b):
 
 @pytest.mark.parametrize("name", ["tiny", "medium_0.0123", "assignment", "medium_full"])
 @pytest.mark.parametrize("kind,ell,omega", [(0, 1, 1.0), (0, 3, 1.2), (1, 2, 0.9)])
-def test_sweep_parity(lpk, ctx, orc, name, kind, ell, omega):
+def test_sweep_parity(lpk, pctx, orc, name, kind, ell, omega):
     lp = gen.medium_lp() if name == "medium_full" else LPS[name]()
-    P = lpk.Problem.from_lp(ctx, lp)
+    P = lpk.Problem.from_lp(pctx, lp)
     color, perm, cptr = P.coloring()
     rng = np.random.default_rng(2)
     d2 = np.exp(rng.uniform(-6, 6, lp.n))
@@ -124,9 +141,9 @@ def test_sweep_parity(lpk, ctx, orc, name, kind, ell, omega):
 
 @pytest.mark.parametrize("solver", [0, 1])
 @pytest.mark.parametrize("name", ["tiny", "medium_0.05", "assignment"])
-def test_ne_solve_parity(lpk, ctx, orc, name, solver):
+def test_ne_solve_parity(lpk, pctx, orc, name, solver):
     lp = LPS[name]()
-    P = lpk.Problem.from_lp(ctx, lp)
+    P = lpk.Problem.from_lp(pctx, lp)
     color, perm, cptr = P.coloring()
     rng = np.random.default_rng(3)
     d2 = np.exp(rng.uniform(-3, 3, lp.n))
@@ -147,6 +164,15 @@ def test_ne_solve_parity(lpk, ctx, orc, name, solver):
     assert np.linalg.norm(r) <= 1e-6 * np.linalg.norm(f)
 
 
+_ORACLE_LP = {}
+
+
+def _oracle_lp(orc, name, lp, kw):
+    if name not in _ORACLE_LP:
+        _ORACLE_LP[name] = orc.lp_solve_lp(lp, **kw)
+    return _ORACLE_LP[name]
+
+
 def _lp_case(name):
     if name == "tiny":
         return gen.tiny_lp(), dict(inner_sweeps=1)
@@ -160,12 +186,12 @@ def _lp_case(name):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", ["tiny", "assignment", "medium_0.05"])
-def test_lp_solve_parity(lpk, ctx, orc, name, precision):
+def test_lp_solve_parity(lpk, pctx, orc, name, precision):
     lp, kw = _lp_case(name)
-    P = lpk.Problem.from_lp(ctx, lp)
+    P = lpk.Problem.from_lp(pctx, lp)
     x, y, s, info = P.lp_solve(lp.b, lp.c, precision=precision, **kw)
     assert info["status_name"] == "OK", info
-    ox, oy, os_, oinfo = orc.lp_solve_lp(lp, **kw)
+    ox, oy, os_, oinfo = _oracle_lp(orc, name, lp, kw)
     assert oinfo["status_name"] == "OK"
     ref = oinfo["obj_primal"]
     assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
@@ -234,6 +260,7 @@ def test_full_size_medium_sampled(lpk, ctx, orc):
                                    1.0, 0, 1e-8, lp.m)
     dy, dw, info = P.ne_solve(torch.from_numpy(d2).cuda(), torch.from_numpy(lp.b).cuda(),
                               inner_sweeps=3, tol=1e-8)
+    assert ctx.stats()["last_cluster_size"] == 16      # the cluster path ran
     assert info["converged"] and oinfo["converged"]
     assert abs(info["iters"] - oinfo["iters"]) <= 2
     assert rel(dw.cpu().numpy(), odw) < 1e-5
