@@ -1051,3 +1051,102 @@ lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int 
   A.out_u = u;
   return launch(ctx, P, A, precision == LPK_MIXED);
 }
+
+// ---------------------------------------------------------------------------
+// Variant for lpk_ne_solve_noalloc: the same persistent kernel with every
+// buffer carved from caller-supplied device memory (ws), no allocation, no
+// events and no pinned host memory.  ws must hold krylov_scratch_doubles()
+// doubles, 256-byte aligned.
+// ---------------------------------------------------------------------------
+size_t krylov_scratch_doubles(const DevProblem &P) {
+  const size_t m = P.m > 0 ? P.m : 1, n = P.n > 0 ? P.n : 1;
+  // workspace (6 m + 6 n), control block (rounded up), partials (8 x 4096)
+  return 6 * m + 6 * n + 64 + 8 * 4096;
+}
+
+lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
+                                const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
+                                KrylovResult *out, double *ws) {
+  if (method != LPK_MRNE && method != LPK_CGNE) {
+    ctx->err = "solver not available in the persistent kernel";
+    return LPK_INVALID_ARG;
+  }
+  const size_t m = P.m > 0 ? P.m : 1, n = P.n > 0 ? P.n : 1;
+  Workspace W;
+  double *b = ws;
+  W.g = b; b += m;
+  W.t = b; b += m;
+  W.qt = b; b += m;
+  W.pt = b; b += m;
+  W.by = b; b += m;
+  W.z = b; b += m;
+  W.q = b; b += n;
+  W.p0 = b; b += n;
+  W.p1 = b; b += n;
+  W.bw = b; b += n;
+  W.u = b; b += n;
+  W.uw = b; b += n;
+  KrylovCtl *ctl = (KrylovCtl *)b;
+  b += 64;
+  double *part = b;
+  KArgs A{};
+  A.m = P.m;
+  A.n = P.n;
+  A.nc = P.n_colors;
+  A.rp = P.rp;
+  A.ci = P.ci;
+  A.cptr = P.color_ptr;
+  A.a64 = P.ah64;
+  A.a32 = P.ah32;
+  A.cp = P.cp;
+  A.ri = P.ri;
+  A.aht = P.aht;
+  A.uw = W.uw;
+  A.ell = ell;
+  A.omega = omega;
+  A.g = W.g; A.t = W.t; A.qt = W.qt; A.pt = W.pt; A.by = W.by;
+  A.q = W.q; A.p0 = W.p0; A.p1 = W.p1; A.bw = W.bw;
+  A.u = W.u; A.z = W.z;
+  A.part = part;
+  A.ctl = ctl;
+  A.f = f_hat;
+  A.tol = tol;
+  A.maxit = maxit;
+  A.method = method == LPK_MRNE ? M_MRNE : M_CGNE;
+  A.wy = precision == LPK_MIXED ? 1 : 0;
+  A.max_restarts = 3;
+  A.dw = dw;
+  A.dy = dy_hat;
+  A.hist = nullptr;
+  // grid path only: one CTA per SM, cooperative launch
+  const int f32 = precision == LPK_MIXED;
+  void *gfn = kernel_for<GridGrp>(A.method, f32);
+  int rw = 0;
+  const size_t gsmem = zstore_bytes(P, ctx->num_sms * KWPB, &rw);
+  if (gsmem > SMEM_LIMIT) {
+    ctx->err = "too many colors for the shared-memory sweep state";
+    return LPK_INVALID_ARG;
+  }
+  LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+  A.rw = rw;
+  A.z_off = 0;
+  A.u_shift = 0;
+  LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(KrylovCtl), ctx->stream));
+  void *args[] = {&A};
+  LPK_COUNT(ctx);
+  LPK_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(gfn, dim3(ctx->num_sms), dim3(KTPB), args, gsmem, ctx->stream));
+  KrylovCtl h;
+  LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&h, ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, ctx->stream));
+  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h.status == LPK_TIMEOUT) {
+    ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out";
+    return LPK_TIMEOUT;
+  }
+  out->iters = h.iters;
+  out->converged = h.converged;
+  out->restarts = h.restarts;
+  out->breakdown = h.breakdown;
+  out->res0 = h.res0;
+  out->res = h.res;
+  return LPK_OK;
+}

@@ -184,3 +184,8 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
                         KrylovResult *out, double *hist);
 lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int ell, double omega,
                       const double *g_hat, double *z, double *u);
+// persistent Krylov solve on caller-supplied device memory (no allocation)
+size_t krylov_scratch_doubles(const DevProblem &P);
+lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
+                                const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
+                                KrylovResult *out, double *ws);

@@ -29,7 +29,7 @@ NE_SSOR, NE_SOR = 0, 1
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
            "lpk_reset_stats", "lpk_set_exec", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
-           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_lp_solve"]
+           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_lp_solve"]
 
 
 class LpkError(RuntimeError):
@@ -112,6 +112,8 @@ def load():
         "lpk_sweep": (I32, [P, P, P, P, I32, I32, D, I32, P, P, I32]),
         "lpk_ne_solve": (I32, [P, P, P, P, I32, D, I32, I32, D, I32, P, P, C.POINTER(KrylovInfo), I32]),
         "lpk_lp_solve": (I32, [P, P, P, P, C.POINTER(Options), P, P, P, C.POINTER(Info), I32]),
+        "lpk_ne_solve_noalloc": (I32, [P, P, P, P, I32, D, I32, I32, D, I32, P, P,
+                                       C.POINTER(KrylovInfo)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -317,6 +319,16 @@ class Problem:
                                                     max_iter, _ptr(dy)[0], _ptr(dw)[0],
                                                     C.byref(ki), dev))
         return dy, dw, ki.as_dict()
+
+    def ne_solve_noalloc(self, d2, f, dy, dw=None, inner_sweeps=1, omega=1.0, solver=MRNE,
+                         precision=FP64, tol=1e-10, max_iter=0):
+        """lpk_ne_solve_noalloc: device tensors in and out (dy, dw preallocated by
+        the caller); the library allocates nothing.  Returns the info dict."""
+        ki = KrylovInfo()
+        _check(self.ctx.handle, load().lpk_ne_solve_noalloc(
+            self.ctx.handle, self._h, _ptr(d2)[0], _ptr(f)[0], inner_sweeps, omega, solver, precision,
+            tol, max_iter, _ptr(dy)[0], _ptr(dw)[0], C.byref(ki)))
+        return ki.as_dict()
 
     def lp_solve(self, b, c, options: Options | None = None, out=None, **kw):
         """Returns (x[n], y[m], s[n], info dict).  Status codes other than OK,
