@@ -146,7 +146,7 @@ typedef struct lpk_stats {
   int64_t csc_passes;
   int64_t barriers;
   int32_t last_cluster_size;  /* 0: the last Krylov launch used the grid path */
-  int32_t reserved;
+  int32_t last_resident;      /* 1: it kept every warp's rows in shared memory */
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.
@@ -156,8 +156,16 @@ typedef struct lpk_stats {
  *  LPK_EXEC_GRID:    every SM, software grid barrier, u in global memory.
  *  LPK_EXEC_CLUSTER: the cluster path (LPK_INVALID_ARG at solve time if u does
  *                    not fit).
+ * Or-ing LPK_EXEC_NO_RESIDENT disables the shared-memory row cache (by
+ * default each warp keeps the column indices and values of its rows in shared
+ * memory for the whole launch when they fit).
  * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
-typedef enum lpk_exec { LPK_EXEC_AUTO = 0, LPK_EXEC_GRID = 1, LPK_EXEC_CLUSTER = 2 } lpk_exec;
+typedef enum lpk_exec {
+  LPK_EXEC_AUTO = 0,
+  LPK_EXEC_GRID = 1,
+  LPK_EXEC_CLUSTER = 2,
+  LPK_EXEC_NO_RESIDENT = 4
+} lpk_exec;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  The context owns its

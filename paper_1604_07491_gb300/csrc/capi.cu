@@ -142,11 +142,14 @@ LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out) {
   if (!ctx || !out) return LPK_INVALID_ARG;
   *out = ctx->stats;
   out->last_cluster_size = ctx->last_cluster;
+  out->last_resident = ctx->last_resident;
   return LPK_OK;
 }
 
 LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size) {
   if (!ctx) return LPK_INVALID_ARG;
+  const int no_res = (exec & LPK_EXEC_NO_RESIDENT) != 0;
+  exec &= ~LPK_EXEC_NO_RESIDENT;
   if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_CLUSTER ||
       !(cluster_size == 0 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8 || cluster_size == 16)) {
     ctx->err = "lpk_set_exec: exec must be 0..2 and cluster_size 0, 2, 4, 8 or 16";
@@ -154,6 +157,7 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
   }
   ctx->cluster_mode = exec;
   ctx->cluster_size_override = cluster_size;
+  ctx->resident_mode = no_res;
   return LPK_OK;
 }
 

@@ -40,6 +40,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdio>
+#include <vector>
 
 #include "lpk_internal.cuh"
 
@@ -50,6 +51,7 @@ namespace {
 constexpr int KTPB = 256;
 constexpr int KWPB = KTPB / 32;
 constexpr int RC = 4;                 // row entries per lane kept in registers
+constexpr int RCR = 8;                // same, rows cached in shared memory
 constexpr unsigned long long TIMEOUT_NS = 5000000000ull;  // 5 s per barrier wait
 constexpr int MAX_CLUSTER = 16;
 constexpr int MAX_SHIFT = 14;         // <= 2^14 doubles (128 KB) of u per CTA
@@ -82,8 +84,10 @@ struct KArgs {
   int method;
   int max_restarts;
   int u_shift;                     // cluster mode: 2^u_shift entries of u per CTA
-  int rw;                          // z slots per warp in shared memory
-  int z_off;                       // byte offset of the z slots in dynamic shared memory
+  int rw;                          // row slots per warp in shared memory
+  int z_off;                       // byte offsets of the shared-memory blocks (see SmemPlan)
+  int gs_off, desc_off, val_off, rs_off, cum_off, col_off;
+  int resident;                    // rows of each warp cached in shared memory
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
@@ -250,25 +254,52 @@ struct RowPre {
 
 // Per-warp sweep state in shared memory.  The rows of color c handled by warp
 // w are r0(c) + gw + j GW (j = 0, 1, ...); they own the slots
-// cum_w[c] + j of the warp's arrays: z (row corrections) and the row
-// descriptors (k0, len), built once per launch so no row pointer is read on
-// the critical path.
+// cum_w[c] + j of the warp's arrays: z (row corrections), the row
+// descriptors (k0, len) -- or, when the rows are resident, (offset in the
+// warp's entry cache, len) --, the row index, and (resident) g_r.  Built once
+// per launch, so no row pointer is read on the critical path.
 struct ZStore {
   double *zs;    // [KWPB][rw]
+  double *gs;    // [KWPB][rw]   resident only
   int2 *desc;    // [KWPB][rw]
+  int *rs;       // [KWPB][rw]
   int *cum;      // [KWPB][nc + 1]
+  void *vals;    // [entries of the CTA]   resident only (TV)
+  int *cols;     // [entries of the CTA]   resident only
   int rw, nc;
-  __device__ __forceinline__ double *zw() const { return zs + (threadIdx.x >> 5) * rw; }
-  __device__ __forceinline__ const int2 *dw() const { return desc + (threadIdx.x >> 5) * rw; }
-  __device__ __forceinline__ const int *cw() const { return cum + (threadIdx.x >> 5) * (nc + 1); }
+  __device__ __forceinline__ int wi() const { return threadIdx.x >> 5; }
+  __device__ __forceinline__ double *zw() const { return zs + wi() * rw; }
+  __device__ __forceinline__ double *gw() const { return gs + wi() * rw; }
+  __device__ __forceinline__ const int2 *dw() const { return desc + wi() * rw; }
+  __device__ __forceinline__ const int *rw_rows() const { return rs + wi() * rw; }
+  __device__ __forceinline__ const int *cw() const { return cum + wi() * (nc + 1); }
 };
 
+__device__ __forceinline__ ZStore make_zstore(const KArgs &A) {
+  extern __shared__ __align__(16) char dyn_smem_b[];
+  ZStore Z;
+  Z.zs = (double *)(dyn_smem_b + A.z_off);
+  Z.gs = (double *)(dyn_smem_b + A.gs_off);
+  Z.desc = (int2 *)(dyn_smem_b + A.desc_off);
+  Z.rs = (int *)(dyn_smem_b + A.rs_off);
+  Z.cum = (int *)(dyn_smem_b + A.cum_off);
+  Z.vals = (void *)(dyn_smem_b + A.val_off);
+  Z.cols = (int *)(dyn_smem_b + A.col_off);
+  Z.rw = A.rw;
+  Z.nc = A.nc;
+  return Z;
+}
+
+// Called by every thread of the CTA (contains __syncthreads).
+template <typename TV>
 __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int gw, int GW) {
+  __shared__ int s_wtot[KWPB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *cw = Z.cum + w * (Z.nc + 1);
+  int2 *dw = Z.desc + w * Z.rw;
+  int *rsw = Z.rs + w * Z.rw;
   // warp-parallel prefix sum of the per-color row counts of this warp
-  const int lane = threadIdx.x & 31;
-  int *cw = Z.cum + (threadIdx.x >> 5) * (Z.nc + 1);
-  int2 *dw = Z.desc + (threadIdx.x >> 5) * Z.rw;
-  int carry = 0;
+  int carry = 0, ent = 0;
   for (int base = 0; base < Z.nc; base += 32) {
     const int c = base + lane;
     int cnt = 0, r0 = 0;
@@ -288,13 +319,40 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
       cw[c] = first;
       for (int j = 0; j < cnt; ++j) {
         const int r = r0 + gw + j * GW;
-        const int k0 = __ldg(A.rp + r);
-        dw[first + j] = make_int2(k0, __ldg(A.rp + r + 1) - k0);
+        const int k0 = __ldg(A.rp + r), len = __ldg(A.rp + r + 1) - k0;
+        dw[first + j] = make_int2(k0, len);
+        rsw[first + j] = r;
+        ent += len;
       }
     }
     carry += __shfl_sync(0xffffffffu, incl, 31);
   }
   if (lane == 0) cw[Z.nc] = carry;
+  if (!A.resident) {
+    __syncwarp();
+    return;
+  }
+  // resident rows: this warp's entries go to [base_w, base_w + ent_w) of the
+  // CTA's cache, slot by slot; descriptors switch to cache offsets
+  ent = warp_sum(ent);
+  if (lane == 0) s_wtot[w] = ent;
+  __syncthreads();
+  int basew = 0;
+  for (int v = 0; v < w; ++v) basew += s_wtot[v];
+  __syncthreads();
+  const TV *a = ahat<TV>(A);
+  TV *vals = (TV *)Z.vals;
+  int off = basew;
+  for (int sl = 0; sl < carry; ++sl) {
+    const int2 kl = dw[sl];
+    for (int t = lane; t < kl.y; t += 32) {
+      Z.cols[off + t] = __ldg(A.ci + kl.x + t);
+      vals[off + t] = __ldg(a + kl.x + t);
+    }
+    __syncwarp();
+    if (lane == 0) dw[sl] = make_int2(off, kl.y);
+    off += kl.y;
+  }
   __syncwarp();
 }
 
@@ -354,6 +412,90 @@ __device__ __forceinline__ double row_update(const GRP &Gp, const KArgs &A, cons
   return d;
 }
 
+// Row update from the shared-memory row cache (resident rows).
+template <typename TV, typename GRP>
+__device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, const int *cols, int e0, int len,
+                                                 double g, double om) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  if (len <= 32 * RCR) {
+    int cv[RCR];
+    double av[RCR], uv[RCR];
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) {
+        cv[e] = cols[e0 + lane + 32 * e];
+        av[e] = (double)vals[e0 + lane + 32 * e];
+      }
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) {
+        uv[e] = Gp.uld(cv[e]);
+        s += av[e] * uv[e];
+      }
+    s = warp_sum(s);
+    const double d = om * (g - s);
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) Gp.ust(cv[e], uv[e] + d * av[e]);
+    return d;
+  }
+  for (int t = lane; t < len; t += 32) s += (double)vals[e0 + t] * Gp.uld(cols[e0 + t]);
+  s = warp_sum(s);
+  const double d = om * (g - s);
+  for (int t = lane; t < len; t += 32) {
+    const int c = cols[e0 + t];
+    Gp.ust(c, Gp.uld(c) + d * (double)vals[e0 + t]);
+  }
+  return d;
+}
+
+// inner_sweeps with every row of the warp resident in shared memory: the only
+// global/distributed accesses of a color phase are the gather and scatter of u.
+template <typename TV, typename GRP>
+__device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
+                                 Counters &C, const ZStore &Z) {
+  const int lane = threadIdx.x & 31;
+  const double om = A.omega;
+  const int passes = ssor ? 2 * A.ell : A.ell;
+  const int nc = A.nc;
+  double *zw = Z.zw(), *gsw = Z.gw();
+  const int2 *dw = Z.dw();
+  const int *cw = Z.cw(), *rsw = Z.rw_rows();
+  const TV *vals = (const TV *)Z.vals;
+  const int *cols = Z.cols;
+  const int nslots = cw[nc];
+  for (int sl = lane; sl < nslots; sl += 32) gsw[sl] = ldcg(g + rsw[sl]);  // g once per sweep
+  __syncwarp();
+  C.passes += passes;
+  for (int ps = 0; ps < passes; ++ps) {
+    const bool backward = ssor && (ps & 1);
+    const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+    for (int cc = 0; cc < nc; ++cc) {
+      const int c = backward ? nc - 1 - cc : cc;
+      for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
+        const int2 kl = dw[sl];
+        const double gr = gsw[sl];
+        const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om);
+        if (lane == 0) {
+          const double zn = firstpass ? d : zw[sl] + d;
+          zw[sl] = zn;
+          if (lastpass && acc) *acc += zn * gr;
+        }
+      }
+      if (!(lastpass && cc == nc - 1)) {
+        if (!Gp.sync(s_ok)) return false;
+      }
+    }
+  }
+  __syncwarp();
+  for (int sl = lane; sl < nslots; sl += 32) A.z[rsw[sl]] = zw[sl];
+  if (!acc) {
+    if (!Gp.sync(s_ok)) return false;
+  }
+  return true;
+}
+
 // A full application of the inner iterations on input g (m, double):
 // SSOR (2 passes per sweep) or SOR (1 pass).  u must be zero on entry.  z
 // (row corrections) is kept in shared memory and written to A.z at the end.
@@ -363,6 +505,7 @@ __device__ __forceinline__ double row_update(const GRP &Gp, const KArgs &A, cons
 template <typename TV, typename GRP>
 __device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
                              Counters &C, const ZStore &Z) {
+  if (A.resident) return inner_sweeps_res<TV>(A, Gp, s_ok, g, ssor, acc, C, Z);
   const TV *a = ahat<TV>(A);
   const int lane = threadIdx.x & 31;
   const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
@@ -453,25 +596,22 @@ __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, d
   }
 }
 
-// out = A_hat^T x in double through the CSC (warp per column); returns this
-// thread's share of ||out||^2 and, if old != nullptr, of (old, out) where old
-// is read before out is written (old may alias out)
+// out = A_hat^T x in double through the CSC (thread per column: the columns
+// are short, and independent columns keep many loads in flight); returns
+// this thread's share of ||out||^2 and, if dot_old != nullptr, adds its share
+// of (old, out) where old is read before out is written (old may alias out)
 template <typename GRP>
 __device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, const double *x, double *out,
                                                double *dot_old = nullptr) {
-  const int lane = threadIdx.x & 31;
-  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
+  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
   double acc = 0.0;
-  for (int j = gw; j < A.n; j += GW) {
+  for (int j = tid; j < A.n; j += NT) {
     const int q0 = __ldg(A.cp + j), q1 = __ldg(A.cp + j + 1);
     double s = 0.0;
-    for (int q = q0 + lane; q < q1; q += 32) s += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (dot_old) *dot_old += ldcg(out + j) * s;
-      out[j] = s;
-      acc += s * s;
-    }
+    for (int q = q0; q < q1; ++q) s += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
+    if (dot_old) *dot_old += ldcg(out + j) * s;
+    out[j] = s;
+    acc += s * s;
   }
   return acc;
 }
@@ -498,11 +638,8 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
   const bool cta0 = Gp.rank() == 0 && threadIdx.x == 0;
   const int m = A.m, n = A.n;
   Counters Cn;
-  extern __shared__ double dyn_smem[];
-  char *zbase = (char *)dyn_smem + A.z_off;
-  ZStore Z{(double *)zbase, (int2 *)(zbase + sizeof(double) * KWPB * A.rw),
-           (int *)(zbase + (sizeof(double) + sizeof(int2)) * KWPB * A.rw), A.rw, A.nc};
-  zstore_init(A, Z, Gp.rank() * KWPB + (threadIdx.x >> 5), Gp.size() * KWPB);
+  const ZStore Z = make_zstore(A);
+  zstore_init<TV>(A, Z, Gp.rank() * KWPB + (threadIdx.x >> 5), Gp.size() * KWPB);
   auto uget = [&](int j) { return Gp.uld(j); };
   auto zget = [&](int i) { return ldcg(A.z + i); };
 
@@ -839,26 +976,99 @@ void *kernel_for(int method, int f32) {
   return f32 ? (void *)k_krylov<M_SWEEP, float, GRP> : (void *)k_krylov<M_SWEEP, double, GRP>;
 }
 
-constexpr size_t SMEM_LIMIT = 227 * 1024;
+// dynamic shared memory per CTA: the opt-in maximum (227 KB) minus room for
+// the kernels' static shared memory
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;
 
-// shared memory of the per-warp z slots and color offsets for GW warps
-size_t zstore_bytes(const DevProblem &P, int GW, int *rw) {
-  *rw = (P.m + GW - 1) / GW + P.n_colors;
-  return (sizeof(double) + sizeof(int2)) * KWPB * (size_t)*rw + sizeof(int) * KWPB * (size_t)(P.n_colors + 1);
+// Shared-memory layout of one CTA: [u slice (cluster path)] [z slots]
+// [row descriptors] [row indices] [color offsets] and, when the rows are
+// resident, [g slots] [values] [column indices] of the CTA's rows.
+struct SmemPlan {
+  size_t total = 0;
+  int rw = 0, resident = 0;
+  int z_off = 0, gs_off = 0, desc_off = 0, val_off = 0, rs_off = 0, cum_off = 0, col_off = 0;
+};
+
+// nonzeros of the busiest CTA when ctas x KWPB warps take the rows color by color
+long long max_cta_entries(const DevProblem &P, int ctas) {
+  const int GW = ctas * KWPB;
+  std::vector<long long> per(ctas, 0);
+  for (int c = 0; c < P.n_colors; ++c) {
+    const int r0 = P.color_ptr_h[c], r1 = P.color_ptr_h[c + 1];
+    for (int i = 0; i < r1 - r0; ++i) per[(i % GW) / KWPB] += P.rp_h[r0 + i + 1] - P.rp_h[r0 + i];
+  }
+  long long mx = 0;
+  for (long long v : per) mx = v > mx ? v : mx;
+  return mx;
+}
+
+SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident) {
+  SmemPlan L;
+  const int GW = ctas * KWPB;
+  L.rw = (P.m + GW - 1) / GW + P.n_colors;
+  size_t off = u_bytes;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 15) & ~size_t(15);
+    return (int)o;
+  };
+  L.z_off = take(sizeof(double) * KWPB * (size_t)L.rw);
+  L.desc_off = take(sizeof(int2) * KWPB * (size_t)L.rw);
+  L.rs_off = take(sizeof(int) * KWPB * (size_t)L.rw);
+  L.cum_off = take(sizeof(int) * KWPB * (size_t)(P.n_colors + 1));
+  L.total = off;
+  if (allow_resident && (long long)P.rp_h.size() == (long long)P.m + 1) {
+    const long long ent = max_cta_entries(P, ctas);
+    const int gs = take(sizeof(double) * KWPB * (size_t)L.rw);
+    const int vo = take((size_t)vbytes * ent);
+    const int co = take(sizeof(int) * ent);
+    if (off <= SMEM_LIMIT) {
+      L.resident = 1;
+      L.gs_off = gs;
+      L.val_off = vo;
+      L.col_off = co;
+      L.total = off;
+    }
+  }
+  return L;
+}
+
+void apply_plan(KArgs &A, const SmemPlan &L) {
+  A.rw = L.rw;
+  A.resident = L.resident;
+  A.z_off = L.z_off;
+  A.gs_off = L.gs_off;
+  A.desc_off = L.desc_off;
+  A.val_off = L.val_off;
+  A.rs_off = L.rs_off;
+  A.cum_off = L.cum_off;
+  A.col_off = L.col_off;
 }
 
 // Cluster size and u slice (2^shift doubles per CTA) for a problem, or 0 when
 // the grid path is used.  The cluster path keeps u (n doubles) in the CTAs'
 // shared memory.
+// effective path: the context's setting, or the autotuned one in auto mode
+void exec_mode(lpk_ctx *ctx, const DevProblem &P, int *mode, int *csov) {
+  *mode = ctx->cluster_mode;
+  *csov = ctx->cluster_size_override;
+  if (*mode == 0 && P.tuned) {
+    *mode = P.tuned_mode;
+    *csov = P.tuned_cs;
+  }
+}
+
 int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int *shift) {
-  if (ctx->cluster_mode == 1 || P.n <= 0) return 0;  // forced grid
+  int mode, csov;
+  exec_mode(ctx, P, &mode, &csov);
+  if (mode == 1 || P.n <= 0) return 0;  // grid
   int cs = 2;
   while (cs < MAX_CLUSTER && (long long)cs * 16384 < P.nnz) cs *= 2;
-  if (ctx->cluster_size_override > 0) cs = ctx->cluster_size_override;
+  if (csov > 0) cs = csov;
   int s = 5;
   while ((1ll << s) * cs < P.n) ++s;
   if (s > MAX_SHIFT) {
-    if (ctx->cluster_mode == 2) return -1;  // forced cluster impossible
+    if (mode == 2) return -1;  // forced cluster impossible
     return 0;
   }
   *shift = s;
@@ -889,9 +1099,8 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       int s2 = shift;
       while ((1ll << s2) * use_cs < P.n) ++s2;
       if (s2 > MAX_SHIFT) { use_cs = 0; break; }
-      int rw = 0;
-      const size_t zb = zstore_bytes(P, use_cs * KWPB, &rw);
-      smem = (sizeof(double) << s2) + zb;
+      const SmemPlan L = plan_smem(P, use_cs, sizeof(double) << s2, f32 ? 4 : 8, ctx->resident_mode == 0);
+      smem = L.total;
       if (smem > SMEM_LIMIT) continue;
       LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeNonPortableClusterSizeAllowed, use_cs > 8 ? 1 : 0));
@@ -909,14 +1118,15 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       if (cudaOccupancyMaxActiveClusters(&nclusters, cfn, &cfg) == cudaSuccess && nclusters > 0) {
         shift = s2;
         A.u_shift = s2;
-        A.rw = rw;
-        A.z_off = (int)(sizeof(double) << s2);
+        apply_plan(A, L);
         break;
       }
       cudaGetLastError();
     }
     if (use_cs < 2) use_cs = 0;
-    if (use_cs == 0 && ctx->cluster_mode == 2) {
+    int emode, ecs;
+    exec_mode(ctx, P, &emode, &ecs);
+    if (use_cs == 0 && emode == 2) {
       ctx->err = "no cluster configuration of the persistent kernel can be scheduled";
       return LPK_CUDA_ERROR;
     }
@@ -925,8 +1135,8 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   size_t gsmem = 0;
   if (use_cs == 0) {
     gfn = kernel_for<GridGrp>(A.method, f32);
-    int rw = 0;
-    gsmem = zstore_bytes(P, ctx->num_sms * KWPB, &rw);
+    const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0);
+    gsmem = L.total;
     if (gsmem > SMEM_LIMIT) {
       ctx->err = "too many colors for the shared-memory sweep state";
       return LPK_INVALID_ARG;
@@ -938,10 +1148,10 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       ctx->err = "persistent Krylov kernel does not fit on an SM";
       return LPK_CUDA_ERROR;
     }
-    A.rw = rw;
-    A.z_off = 0;
+    apply_plan(A, L);
     A.u_shift = 0;
   }
+  ctx->last_resident = A.resident;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->kctl, 0, sizeof(KrylovCtl), ctx->stream));
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   LPK_COUNT(ctx);
@@ -970,6 +1180,50 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
     ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out";
     return LPK_TIMEOUT;
   }
+  return LPK_OK;
+}
+
+// Autotuner: time a few Krylov iterations of every execution path on the
+// problem's first solve (its actual matrix and right-hand side) and keep the
+// fastest for the problem.  Candidates: grid, clusters of 16, 8 and 4 CTAs
+// (each with the shared-memory row cache when it fits).
+lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
+  const int cands[4][2] = {{1, 0}, {2, 16}, {2, 8}, {2, 4}};
+  const int save_mode = ctx->cluster_mode, save_cs = ctx->cluster_size_override;
+  const lpk_stats save_stats = ctx->stats;
+  double best = 1e300;
+  int bm = 1, bcs = 0;
+  for (int i = 0; i < 4; ++i) {
+    ctx->cluster_mode = cands[i][0];
+    ctx->cluster_size_override = cands[i][1];
+    KArgs A = base;
+    A.maxit = 12;
+    A.tol = 0.0;
+    A.max_restarts = 0;
+    const double ms0 = ctx->stats.krylov_ms;
+    const lpk_status st = launch(ctx, P, A, f32);
+    P.tuned_us[i] = 0.0;
+    if (st == LPK_TIMEOUT) {
+      ctx->cluster_mode = save_mode;
+      ctx->cluster_size_override = save_cs;
+      return st;
+    }
+    if (st != LPK_OK || (cands[i][0] == 2 && ctx->last_cluster != cands[i][1])) continue;
+    const KrylovCtl *h = (const KrylovCtl *)ctx->h_kctl;
+    const double us = 1e3 * (ctx->stats.krylov_ms - ms0) / (h->iters > 0 ? h->iters : 1);
+    P.tuned_us[i] = us;
+    if (us < best) {
+      best = us;
+      bm = cands[i][0];
+      bcs = cands[i][1];
+    }
+  }
+  ctx->cluster_mode = save_mode;
+  ctx->cluster_size_override = save_cs;
+  ctx->stats = save_stats;
+  P.tuned = 1;
+  P.tuned_mode = bm;
+  P.tuned_cs = bcs;
   return LPK_OK;
 }
 
@@ -1023,6 +1277,9 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   A.dw = dw;
   A.dy = dy_hat;
   A.hist = hist;
+  if (ctx->cluster_mode == 0 && !P.tuned && P.m > 0) {
+    if ((st = autotune(ctx, P, A, precision == LPK_MIXED)) != LPK_OK) return st;
+  }
   st = launch(ctx, P, A, precision == LPK_MIXED);
   if (st != LPK_OK) return st;
   const KrylovCtl *h = (const KrylovCtl *)ctx->h_kctl;
@@ -1121,15 +1378,14 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   // grid path only: one CTA per SM, cooperative launch
   const int f32 = precision == LPK_MIXED;
   void *gfn = kernel_for<GridGrp>(A.method, f32);
-  int rw = 0;
-  const size_t gsmem = zstore_bytes(P, ctx->num_sms * KWPB, &rw);
+  const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0);
+  const size_t gsmem = L.total;
   if (gsmem > SMEM_LIMIT) {
     ctx->err = "too many colors for the shared-memory sweep state";
     return LPK_INVALID_ARG;
   }
   LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
-  A.rw = rw;
-  A.z_off = 0;
+  apply_plan(A, L);
   A.u_shift = 0;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(KrylovCtl), ctx->stream));
   void *args[] = {&A};

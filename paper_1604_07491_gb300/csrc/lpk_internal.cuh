@@ -49,6 +49,11 @@ struct DevProblem {
 
   int *color_ptr = nullptr;      // [n_colors+1] device copy
   std::vector<int> color_ptr_h;  // host copy
+  std::vector<int> rp_h;         // host copy of rp (sizes the shared-memory row cache)
+
+  // execution path chosen by the autotuner (first solve on this problem)
+  int tuned = 0, tuned_mode = 0, tuned_cs = 0;
+  double tuned_us[4] = {0, 0, 0, 0};  // time per Krylov iteration of grid, cluster 16, 8, 4
 
   // Krylov workspace (allocated on first use)
   size_t ws_bytes = 0;
@@ -85,6 +90,8 @@ struct lpk_ctx {
   int cluster_mode = 0;          // 0 auto, 1 grid, 2 cluster
   int cluster_size_override = 0; // 0: chosen from nnz
   int last_cluster = 0;          // cluster size of the last launch (0: grid)
+  int resident_mode = 0;         // 0: rows cached in shared memory when they fit, 1: never
+  int last_resident = 0;         // the last launch cached the rows
 
   // problems prepared on this context (freed with it)
   std::vector<lpk_problem *> problems;

@@ -499,6 +499,8 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dmalloc(&P.in_row_of_pos, mr));
   if (m > 0) LPK_LAUNCH(ctx, k_compose, nblk(m), TPB, 0, st, m, row_map, pos_of_red, color, P.pos_of_in_row, P.color_in);
   if (mr > 0) LPK_LAUNCH(ctx, k_inrow_of_pos, nblk(mr), TPB, 0, st, mr, perm, red_row, P.in_row_of_pos);
+  P.rp_h.assign(mr + 1, 0);
+  LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.rp_h.data(), P.rp, sizeof(int) * (mr + 1), cudaMemcpyDeviceToHost, st));
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   return LPK_OK;

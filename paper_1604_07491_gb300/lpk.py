@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREA
           6: "EMPTY_ROW_INCONSISTENT", 7: "EMPTY_COL_UNBOUNDED", 8: "INVALID_ARG", 9: "OOM",
           10: "CUDA_ERROR"}
 MRNE, CGNE, ABGMRES = 0, 1, 2
-EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER = 0, 1, 2
+EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER, EXEC_NO_RESIDENT = 0, 1, 2, 4
 FP64, MIXED = 0, 1
 NE_SSOR, NE_SOR = 0, 1
 
@@ -77,7 +77,7 @@ class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("krylov_launches", C.c_int64), ("krylov_ms", C.c_double),
                 ("krylov_iters", C.c_int64), ("sweep_passes", C.c_int64), ("row_passes", C.c_int64),
                 ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("last_resident", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
