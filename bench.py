@@ -39,6 +39,9 @@ WORKLOADS = {
 }
 
 
+SOLVERS = {"mrne": 0, "cgne": 1, "abgmres": 2}
+
+
 def make_lp(workload, seed_offset=0):
     from paper_1604_07491_gb300 import gen
     if workload == "medium":
@@ -117,14 +120,17 @@ def algorithmic_bytes(stats, m, n, nnz, precision):
     vector entry (8 + 4 + 8 B) per nonzero, row pointer + result (4 + 8 B) per row.
     CSC pass (w-space image): same per nonzero, 12 B per column.
     Vector work per Krylov iteration: about 12 n-vectors and 12 m-vectors of
-    8 B streamed (updates, fused norms and the p/q recurrences)."""
+    8 B streamed (updates, fused norms and the p/q recurrences).
+    AB-GMRES basis: 8 B per row for every m-row pass over a basis vector
+    (counted by the kernel: four per vector per iteration, one in V p)."""
     vb = 4 if precision == "mixed" else 8
     per_pass = nnz * (vb + 4 + 16) + m * 28
     per_row = nnz * 20 + m * 12
     per_col = nnz * 20 + n * 12
     per_iter = 8 * (12 * n + 12 * m)
     return (stats["sweep_passes"] * per_pass + stats["row_passes"] * per_row
-            + stats["csc_passes"] * per_col + stats["krylov_iters"] * per_iter)
+            + stats["csc_passes"] * per_col + stats["krylov_iters"] * per_iter
+            + stats.get("basis_passes", 0) * 8 * m)
 
 
 def _oracle_kw(opts):
@@ -173,7 +179,9 @@ def run_reference(args):
         return
     wl = WORKLOADS[args.workload]
     lp = make_lp(args.workload)
-    opts = wl["opts"]
+    opts = dict(wl["opts"])
+    if args.solver:
+        opts["solver"] = SOLVERS[args.solver]
     secs, samples = [], []
     for i in range(args.warmup + args.steps):
         sec, sample = oracle_lp_seconds(lp, opts, args.ref_full_krylov)
@@ -203,6 +211,8 @@ def main():
     # for a default run with three warm-up solves
     ap.add_argument("--workload", default="assignment", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--solver", default="", choices=["", "mrne", "cgne", "abgmres"],
+                    help="Krylov solver (default: the workload's)")
     ap.add_argument("--compare-fp64", type=int, default=1, help="also time K FP64 solves")
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
@@ -235,6 +245,8 @@ def main():
 
     wl = WORKLOADS[args.workload]
     opts = dict(wl["opts"])
+    if args.solver:
+        opts["solver"] = SOLVERS[args.solver]
     prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
     # replicas: each rank solves its own LP of the same family (weak scaling)
     lp = make_lp(args.workload, seed_offset=rank)

@@ -147,6 +147,9 @@ typedef struct lpk_stats {
   int64_t barriers;
   int32_t last_cluster_size;  /* 0: the last Krylov launch used the grid path */
   int32_t last_resident;      /* 1: it kept every warp's rows in shared memory */
+  int64_t basis_passes;       /* AB-GMRES: m-row passes over one basis vector
+                                 (four per vector and iteration in the two
+                                 Gram-Schmidt passes, one per vector in V p) */
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.

@@ -39,6 +39,8 @@
 // product so dw and dy stay consistent to FP64 rounding.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -56,8 +58,8 @@ constexpr unsigned long long TIMEOUT_NS = 5000000000ull;  // 5 s per barrier wai
 constexpr int MAX_CLUSTER = 16;
 constexpr int MAX_SHIFT = 14;         // <= 2^14 doubles (128 KB) of u per CTA
 
-enum { M_MRNE = 0, M_CGNE = 1, M_SWEEP = 7, M_SWEEP_SSOR = 8, M_SWEEP_SOR = 9 };
-enum { EXIT_CONV = 0, EXIT_MAXIT = 1, EXIT_BREAK = 2 };
+enum { M_MRNE = 0, M_CGNE = 1, M_ABG = 2, M_SWEEP = 7, M_SWEEP_SSOR = 8, M_SWEEP_SOR = 9 };
+enum { EXIT_CONV = 0, EXIT_MAXIT = 1, EXIT_BREAK = 2, EXIT_CYCLE = 3 };
 
 struct KrylovCtl {
   unsigned long long bar;
@@ -65,6 +67,7 @@ struct KrylovCtl {
   int iters, restarts, converged, breakdown, pad;
   double res0, res;
   long long passes, rows, cols, barriers;   // work counters of the launch
+  long long basis;                          // AB-GMRES basis-vector passes
 };
 
 struct KArgs {
@@ -96,6 +99,14 @@ struct KArgs {
   KrylovCtl *ctl;
   double *hist;
   double *out_z, *out_u;           // sweep-only mode outputs
+  // AB-GMRES (Algorithm 4): basis V [m x ldv] (row-major: the kmax + 1
+  // basis entries of one row are contiguous), R of the rotated Hessenberg
+  // matrix packed by columns (column j holds rows 0..j), Givens cs/sn, rotated
+  // right-hand side gh, Gram-Schmidt coefficients h1/h2 of the two passes,
+  // least-squares solution pv, work vector w (m), partial dot products
+  // [CTAs x ldv]
+  double *V, *R, *cs, *sn, *gh, *h1, *h2, *pv, *wt, *gpart;
+  int kmax, ldv;
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -111,7 +122,7 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 
 // work counters (every thread keeps identical copies; CTA 0 reports them)
 struct Counters {
-  long long passes = 0, rows = 0, cols = 0;
+  long long passes = 0, rows = 0, cols = 0, basis = 0;
 };
 
 // ---- group policies --------------------------------------------------------
@@ -786,6 +797,168 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         gnorm = sqrt(w[1]);
         if (A.hist && cta0) A.hist[k] = gnorm;
       }
+    } else if (METH == M_ABG) {
+      // ---- Algorithm 4: AB-GMRES with NE-SOR inner iterations ----------------
+      // V is row-major [m x ldv]: row r holds (v_0)_r, (v_1)_r, ..., so both the
+      // dot products (threads over basis vectors) and the updates (a warp over
+      // one row's coefficients) read contiguous memory.  Orthogonalisation is
+      // classical Gram-Schmidt with one reorthogonalisation (two passes, each a
+      // dot-product phase and an update phase).  Each CTA owns the rows
+      // [rlo, rhi) in these phases.  The sweep runs on the unnormalised vector
+      // (w, or g at a cycle start); by linearity of the NE-SOR operator the
+      // product A_hat B v = (A_hat B w) / h, so the normalisation is folded
+      // into the next product and costs no barrier.
+      const int G = Gp.size(), b = Gp.rank();
+      const int RB = (m + G - 1) / G, rlo = min(m, b * RB), rhi = min(m, rlo + RB);
+      const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+      const size_t ld = (size_t)A.ldv;
+      double ghk = gnorm;          // rotated right-hand side entry of the newest row
+      double hs = gnorm;           // norm of the vector the next sweep runs on
+      const double *vin = A.g;     // that vector (unnormalised)
+      if (cta0) A.gh[0] = gnorm;
+      int kk = 0;                  // basis vectors of this cycle
+      __shared__ double s_rot[2];
+      while (true) {
+        if (gnorm <= target) { reason = EXIT_CONV; break; }
+        if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
+        if (kk >= A.kmax) { reason = EXIT_CYCLE; break; }
+        // z_k = B v_k (u is zero here)
+        if (!inner_sweeps<TV>(A, Gp, &s_ok, vin, false, nullptr, Cn, Z)) return;
+        const double *uwv = A.uw;
+        if (A.wy) {  // B = A_hat^T C: w-space image in FP64
+          ++Cn.cols;
+          csc_products(Gp, A, A.z, A.uw);
+          if (!Gp.sync(&s_ok)) return;
+        }
+        // v_kk = vin / hs and w = A_hat u / hs on this CTA's rows
+        ++Cn.rows;
+        const double ihs = 1.0 / hs;
+        for (int r = rlo + wi; r < rhi; r += KWPB) {
+          const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
+          double sacc = 0.0;
+          for (int q = k0 + lane; q < k1; q += 32) {
+            const int c = __ldg(A.ci + q);
+            sacc += __ldg(A.a64 + q) * (A.wy ? ldcg(uwv + c) : Gp.uld(c));
+          }
+          sacc = warp_sum(sacc);
+          if (lane == 0) {
+            A.V[(size_t)r * ld + kk] = ldcg(vin + r) * ihs;
+            A.wt[r] = sacc * ihs;
+          }
+        }
+        __syncthreads();
+        double wn2 = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          double *h = pass == 0 ? A.h1 : A.h2;
+          // partial dots (w, v_i) over this CTA's rows, thread per basis vector
+          for (int i = threadIdx.x; i <= kk; i += blockDim.x) {
+            double acc = 0.0;
+            for (int r = rlo; r < rhi; ++r) acc += ldcg(A.wt + r) * ldcg(A.V + (size_t)r * ld + i);
+            A.gpart[(size_t)b * ld + i] = acc;
+          }
+          if (!Gp.sync(&s_ok)) return;
+          // h_i = sum of the G partials in CTA order, spread over all threads
+          for (int i = tid; i <= kk; i += NT) {
+            double acc = 0.0;
+            for (int t = 0; t < G; ++t) acc += ldcg(A.gpart + (size_t)t * ld + i);
+            h[i] = acc;
+          }
+          if (!Gp.sync(&s_ok)) return;
+          // w -= V h on this CTA's rows (a warp per row)
+          double part = 0.0;
+          for (int r = rlo + wi; r < rhi; r += KWPB) {
+            double sacc = 0.0;
+            for (int i = lane; i <= kk; i += 32) sacc += ldcg(h + i) * ldcg(A.V + (size_t)r * ld + i);
+            sacc = warp_sum(sacc);
+            if (lane == 0) {
+              const double w = ldcg(A.wt + r) - sacc;
+              A.wt[r] = w;
+              part += w * w;
+            }
+          }
+          if (pass == 0) {
+            __syncthreads();  // this CTA's rows of w are final before the second pass reads them
+          } else {
+            Gp.uzero(n);      // for the next sweep
+            double v1[1] = {part};
+            put_partials<1>(Gp, v1, A.part, sred);
+            if (!Gp.sync(&s_ok)) return;
+            get_sums<1>(Gp, v1, A.part, sred);
+            wn2 = v1[0];
+          }
+        }
+        Cn.basis += 4 * (kk + 1);  // two passes, each a dot product and an update
+        const double hk1 = sqrt(wn2);
+        // Givens rotations on column kk of H_bar, computed identically in every
+        // CTA; CTA 0 stores R (packed by columns), cs, sn and the rotated rhs
+        if (threadIdx.x == 0) {
+          double *Rc = A.R + (size_t)kk * (kk + 1) / 2;
+          double hprev = ldcg(A.h1) + ldcg(A.h2);
+          for (int i = 0; i < kk; ++i) {
+            const double hn = ldcg(A.h1 + i + 1) + ldcg(A.h2 + i + 1);
+            const double c = ldcg(A.cs + i), sg = ldcg(A.sn + i);
+            const double r0 = c * hprev + sg * hn;
+            hprev = -sg * hprev + c * hn;
+            if (b == 0) Rc[i] = r0;
+          }
+          const double rr = hypot(hprev, hk1);
+          double c = 0.0, sg = 0.0;
+          if (rr > 0.0) { c = hprev / rr; sg = hk1 / rr; }
+          const double ghn = -sg * ghk;
+          if (b == 0) {
+            Rc[kk] = rr;
+            A.cs[kk] = c;
+            A.sn[kk] = sg;
+            A.gh[kk] = c * ghk;
+            A.gh[kk + 1] = ghn;
+          }
+          s_rot[0] = ghn;
+          s_rot[1] = rr;
+        }
+        __syncthreads();
+        const double ghn = s_rot[0], rr = s_rot[1];
+        if (!(rr > 0.0) || !isfinite(rr)) { reason = EXIT_BREAK; break; }
+        ghk = ghn;
+        ++kk;
+        ++k;
+        gnorm = fabs(ghn);
+        if (A.hist && cta0) A.hist[k] = gnorm;
+        if (hk1 == 0.0) { reason = EXIT_CONV; break; }  // lucky breakdown: exact
+        vin = A.wt;
+        hs = hk1;
+      }
+      if (kk > 0) {  // also after a breakdown: the kk completed columns stand
+        // p = R^-1 gh by column-oriented back substitution in CTA 0
+        if (b == 0) {
+          for (int i = threadIdx.x; i < kk; i += blockDim.x) A.pv[i] = ldcg(A.gh + i);
+          __syncthreads();
+          for (int j = kk - 1; j >= 0; --j) {
+            const double *Rc = A.R + (size_t)j * (j + 1) / 2;
+            const double pj = ldcg(A.pv + j) / ldcg(Rc + j);
+            __syncthreads();  // every thread has read pv[j] before it is overwritten
+            for (int i = threadIdx.x; i < j; i += blockDim.x) A.pv[i] = ldcg(A.pv + i) - ldcg(Rc + i) * pj;
+            if (threadIdx.x == 0) A.pv[j] = pj;
+            __syncthreads();
+          }
+        }
+        Gp.uzero(n);
+        if (!Gp.sync(&s_ok)) return;
+        Cn.basis += kk;
+        // q = V p on this CTA's rows
+        for (int r = rlo + wi; r < rhi; r += KWPB) {
+          double sacc = 0.0;
+          for (int i = lane; i < kk; i += 32) sacc += ldcg(A.pv + i) * ldcg(A.V + (size_t)r * ld + i);
+          sacc = warp_sum(sacc);
+          if (lane == 0) A.t[r] = sacc;
+        }
+        if (!Gp.sync(&s_ok)) return;
+        // dw += B q: one more NE-SOR application; its row corrections give dy
+        if (!inner_sweeps<TV>(A, Gp, &s_ok, A.t, false, nullptr, Cn, Z)) return;
+        if (!A.wy)
+          for (int j = tid; j < n; j += NT) A.dw[j] = ldcg(A.dw + j) + uget(j);
+        for (int i = tid; i < m; i += NT) A.dy[i] = ldcg(A.dy + i) + zget(i);
+        if (!Gp.sync(&s_ok)) return;
+      }
     } else {  // CGNE
       // z0 = C g0, u0 = A^T z0, gamma0 = (g0, z0)
       double acc[1] = {0.0};
@@ -910,7 +1083,11 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       for (int j = tid; j < n; j += NT) A.bw[j] = ldcg(A.dw + j);
       for (int i = tid; i < m; i += NT) A.by[i] = ldcg(A.dy + i);
     }
-    if (res <= target || reason != EXIT_CONV || restarts >= A.max_restarts || k >= A.maxit) {
+    // a full AB-GMRES basis (EXIT_CYCLE) restarts from the explicit residual
+    // without counting as a verification restart
+    const bool cycle = reason == EXIT_CYCLE;
+    if (res <= target || (reason != EXIT_CONV && !cycle) || (!cycle && restarts >= A.max_restarts) ||
+        k >= A.maxit) {
       if (cta0) {
         A.ctl->res = res;
         A.ctl->converged = res <= target;
@@ -918,12 +1095,13 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       }
       break;
     }
-    ++restarts;
+    if (!cycle) ++restarts;
   }
   if (cta0) {
     A.ctl->passes = Cn.passes;
     A.ctl->rows = Cn.rows;
     A.ctl->cols = Cn.cols;
+    A.ctl->basis = Cn.basis;
     A.ctl->barriers = Gp.barriers();
     A.ctl->iters = k;
     A.ctl->restarts = restarts;
@@ -961,6 +1139,64 @@ lpk_status get_ws(lpk_ctx *ctx, DevProblem &P, Workspace &W) {
   return LPK_OK;
 }
 
+// AB-GMRES storage of a problem: basis, R, rotations and partial dots, sized
+// for kmax basis vectors.  The paper runs AB-GMRES without restarts; kmax is
+// the iteration cap unless the storage would exceed GM_BUDGET (or half the
+// free device memory), in which case the basis restarts every kmax iterations.
+constexpr size_t GM_BUDGET = size_t(16) << 30;
+
+size_t gm_doubles(size_t m, size_t kmax, size_t ctas, size_t *ld) {
+  *ld = (kmax + 1 + 3) & ~size_t(3);
+  return *ld * (m + 6 + ctas) + kmax * (kmax + 1) / 2 + ((m + 3) & ~size_t(3));
+}
+
+lpk_status get_gmres(lpk_ctx *ctx, DevProblem &P, int maxit, KArgs &A) {
+  const size_t m = P.m > 0 ? P.m : 1, S = (size_t)ctx->num_sms > 16 ? (size_t)ctx->num_sms : 16;
+  size_t kmax = maxit > 0 ? (size_t)maxit : 1, ld = 0;
+  size_t free_b = 0, total_b = 0;
+  LPK_CUDA_TRY(ctx, cudaMemGetInfo(&free_b, &total_b));
+  const size_t budget = std::min(GM_BUDGET, (free_b + P.gm_bytes) / 2) / sizeof(double);
+  if (gm_doubles(m, kmax, S, &ld) > budget) {
+    // largest kmax with kmax^2 / 2 + kmax (m + 6 + S) <= budget, with margin
+    const double a = (double)(m + 7 + S);
+    const double kk = -a + std::sqrt(a * a + 2.0 * (double)budget);
+    kmax = kk > 8.0 ? (size_t)kk - 4 : 0;
+    while (kmax > 0 && gm_doubles(m, kmax, S, &ld) > budget) --kmax;
+    if (kmax < 4) {
+      ctx->err = "not enough device memory for the AB-GMRES basis";
+      return LPK_OOM;
+    }
+  }
+  const size_t need = gm_doubles(m, kmax, S, &ld);
+  if (P.gm_kmax < kmax || P.gm_m != m) {
+    if (P.gm_V) cudaFree(P.gm_V);
+    P.gm_V = nullptr;
+    P.gm_bytes = 0;
+    P.gm_kmax = 0;
+    LPK_CUDA_TRY(ctx, cudaMalloc(&P.gm_V, need * sizeof(double)));
+    P.gm_bytes = need * sizeof(double);
+    P.gm_kmax = kmax;
+    P.gm_m = m;
+  }
+  // carve with the allocation's own kmax (>= kmax): the layout is fixed by ld
+  const size_t kc = P.gm_kmax;
+  gm_doubles(m, kc, S, &ld);
+  double *b = P.gm_V;
+  A.V = b; b += ld * m;
+  A.cs = b; b += ld;
+  A.sn = b; b += ld;
+  A.gh = b; b += ld;
+  A.h1 = b; b += ld;
+  A.h2 = b; b += ld;
+  A.pv = b; b += ld;
+  A.gpart = b; b += ld * S;
+  A.wt = b; b += (m + 3) & ~size_t(3);
+  A.R = b;
+  A.ldv = (int)ld;
+  A.kmax = (int)kmax;
+  return LPK_OK;
+}
+
 lpk_status ensure_kctl(lpk_ctx *ctx) {
   if (ctx->kctl) return LPK_OK;
   LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->kctl, sizeof(KrylovCtl)));
@@ -973,6 +1209,7 @@ template <typename GRP>
 void *kernel_for(int method, int f32) {
   if (method == M_MRNE) return f32 ? (void *)k_krylov<M_MRNE, float, GRP> : (void *)k_krylov<M_MRNE, double, GRP>;
   if (method == M_CGNE) return f32 ? (void *)k_krylov<M_CGNE, float, GRP> : (void *)k_krylov<M_CGNE, double, GRP>;
+  if (method == M_ABG) return f32 ? (void *)k_krylov<M_ABG, float, GRP> : (void *)k_krylov<M_ABG, double, GRP>;
   return f32 ? (void *)k_krylov<M_SWEEP, float, GRP> : (void *)k_krylov<M_SWEEP, double, GRP>;
 }
 
@@ -1175,6 +1412,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   ctx->stats.row_passes += h->rows;
   ctx->stats.csc_passes += h->cols;
   ctx->stats.barriers += h->barriers;
+  ctx->stats.basis_passes += h->basis;
   ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
     ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out";
@@ -1256,8 +1494,8 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
 lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
                         const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
                         KrylovResult *out, double *hist) {
-  if (method != LPK_MRNE && method != LPK_CGNE) {
-    ctx->err = "solver not available in the persistent kernel";
+  if (method != LPK_MRNE && method != LPK_CGNE && method != LPK_ABGMRES) {
+    ctx->err = "unknown Krylov solver";
     return LPK_INVALID_ARG;
   }
   lpk_status st;
@@ -1268,7 +1506,8 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   A.f = f_hat;
   A.tol = tol;
   A.maxit = maxit;
-  A.method = method == LPK_MRNE ? M_MRNE : M_CGNE;
+  A.method = method == LPK_MRNE ? M_MRNE : method == LPK_CGNE ? M_CGNE : M_ABG;
+  if (A.method == M_ABG && (st = get_gmres(ctx, P, maxit, A)) != LPK_OK) return st;
   // FP64: the paper's recurrences; up to 3 restarts when the explicit residual
   // does not confirm the recurrence.  Mixed: sweeps over the FP32 copy of the
   // scaled matrix with FP64 accumulation, w-space images by FP64 CSC products.
@@ -1325,7 +1564,7 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
                                 const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
                                 KrylovResult *out, double *ws) {
   if (method != LPK_MRNE && method != LPK_CGNE) {
-    ctx->err = "solver not available in the persistent kernel";
+    ctx->err = "the allocation-free solve supports MRNE and CGNE only";
     return LPK_INVALID_ARG;
   }
   const size_t m = P.m > 0 ? P.m : 1, n = P.n > 0 ? P.n : 1;

@@ -58,10 +58,10 @@ struct DevProblem {
   // Krylov workspace (allocated on first use)
   size_t ws_bytes = 0;
   void *ws = nullptr;
-  size_t gm_cap = 0;             // AB-GMRES basis capacity (vectors)
+  // AB-GMRES storage (allocated on first use): one block for the basis, R,
+  // rotations and partial dots, sized for gm_kmax basis vectors of gm_m rows
+  size_t gm_bytes = 0, gm_kmax = 0, gm_m = 0;
   double *gm_V = nullptr;
-  double *gm_Z = nullptr;
-  double *gm_Y = nullptr;
 };
 
 struct lpk_problem {

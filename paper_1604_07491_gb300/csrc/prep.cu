@@ -302,7 +302,7 @@ void free_problem(DevProblem &P) {
   void *ptrs[] = {P.pos_of_in_row, P.in_row_of_pos, P.col_of_in, P.in_col_of, P.color_in, P.rp,
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
-                  P.gm_V,          P.gm_Z,          P.gm_Y};
+                  P.gm_V};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   P = DevProblem();

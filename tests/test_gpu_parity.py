@@ -139,7 +139,7 @@ def test_sweep_parity(lpk, pctx, orc, name, kind, ell, omega):
     assert rel(z32, oz) < 2e-4 and rel(u32, ou) < 2e-4
 
 
-@pytest.mark.parametrize("solver", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1, 2])
 @pytest.mark.parametrize("name", ["tiny", "medium_0.05", "assignment"])
 def test_ne_solve_parity(lpk, pctx, orc, name, solver):
     lp = LPS[name]()
@@ -198,6 +198,81 @@ def test_lp_solve_parity(lpk, pctx, orc, name, precision):
     pinf, dinf, gap = certs(lp, x, y, s)
     assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
     if name == "tiny":   # unique optimum: vectors agree too
+        assert rel(x, ox) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "medium_0.0123", "assignment"])
+def test_abgmres_ne_solve_precisions(lpk, pctx, orc, name, precision):
+    """AB-GMRES (Algorithm 4) with NE-SOR: the GPU's classical Gram-Schmidt
+    with reorthogonalisation against the oracle's modified Gram-Schmidt.  In
+    exact arithmetic both give the same iterates; the iteration counts agree
+    to a few and both reach the tolerance.  Mixed precision sweeps an FP32
+    copy of the scaled matrix (a different, still fixed, preconditioner), so
+    only its residual and the dw = D A^T dy consistency are checked."""
+    lp = gen.medium_lp(0.0123) if name == "medium_0.0123" else LPS[name]()
+    P = lpk.Problem.from_lp(pctx, lp)
+    color, perm, cptr = P.coloring()
+    rng = np.random.default_rng(11)
+    d2 = np.exp(rng.uniform(-4, 4, lp.n))
+    A = lp.scipy()
+    f = A @ (d2 * rng.standard_normal(lp.n))
+    ell = 3 if name == "assignment" else 2
+    tol = 1e-8
+    ody, odw, oinfo = orc.ne_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, f, ell, 1.0,
+                                   2, tol, 10 * lp.m)
+    dy, dw, info = P.ne_solve(d2, f, inner_sweeps=ell, solver=2, precision=precision, tol=tol,
+                              max_iter=10 * lp.m)
+    assert oinfo["converged"] and info["converged"], (oinfo, info)
+    assert info["restarts"] <= 1 and not info["breakdown"]
+    r = f - A @ (d2 * (A.T @ dy))
+    assert np.linalg.norm(r) <= 1e-5 * np.linalg.norm(f)
+    assert rel(dw, np.sqrt(d2) * (A.T @ dy)) < 1e-9
+    if precision == 0:
+        assert abs(info["iters"] - oinfo["iters"]) <= max(1, oinfo["iters"] // 50)
+        assert rel(dw, odw) < 1e-5
+    else:
+        assert info["iters"] <= oinfo["iters"] + max(3, oinfo["iters"] // 10)
+
+
+def test_abgmres_capped_iterations(lpk, ctx, orc):
+    """An iteration cap below convergence: both sides stop after exactly the
+    cap, with the minimum-residual iterate of the Krylov space (GMRES
+    residuals are optimal, so the GPU's residual matches the oracle's)."""
+    lp = gen.medium_lp(0.05)
+    P = lpk.Problem.from_lp(ctx, lp)
+    color, perm, cptr = P.coloring()
+    rng = np.random.default_rng(5)
+    d2 = np.exp(rng.uniform(-5, 5, lp.n))
+    A = lp.scipy()
+    f = A @ (d2 * rng.standard_normal(lp.n))
+    cap = 7
+    ody, odw, oinfo = orc.ne_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, f, 1, 1.0,
+                                   2, 1e-14, cap)
+    dy, dw, info = P.ne_solve(d2, f, inner_sweeps=1, solver=2, tol=1e-14, max_iter=cap)
+    assert info["iters"] == oinfo["iters"] == cap
+    assert not info["converged"] and not oinfo["converged"]
+    assert abs(info["res"] - oinfo["res"]) <= 1e-9 * oinfo["res0"]
+    assert rel(dw, odw) < 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "assignment"])
+def test_lp_solve_abgmres(lpk, pctx, orc, name, precision):
+    lp, kw = _lp_case(name)
+    kw = dict(kw, solver=2)
+    P = lpk.Problem.from_lp(pctx, lp)
+    x, y, s, info = P.lp_solve(lp.b, lp.c, precision=precision, **kw)
+    assert info["status_name"] == "OK", info
+    okw = dict(kw)
+    okw["method"] = okw.pop("solver")
+    ox, oy, os_, oinfo = _oracle_lp(orc, name + "_abg", lp, okw)
+    assert oinfo["status_name"] == "OK"
+    ref = oinfo["obj_primal"]
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
+    pinf, dinf, gap = certs(lp, x, y, s)
+    assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+    if name == "tiny":
         assert rel(x, ox) < 1e-6
 
 
