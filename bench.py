@@ -1,18 +1,25 @@
-"""Benchmark: LP solves per second on a seeded synthetic workload.
+"""Benchmark: LPs solved per second (and per-LP latency) on seeded synthetic
+workloads, through the C ABI.
 
-A step is one complete interior-point solve (Algorithm 1 with the Krylov
-search-direction solves) of one LP whose data is already resident in HBM.
-Prints one JSON line (rank 0).  See the design doc for the workload recipes, the
-algorithmic byte counts behind the roofline figure and the timing rules.
+A step is one batch: B LPs of the workload family (different seeds), each a
+complete interior-point solve (Algorithm 1 with the Krylov search-direction
+solves), run side by side on the GPU (lpk_lp_solve_batch: one context, stream
+and thread-block cluster per LP).  --batch 1 times one LP at a time on the
+autotuned single-LP path.  Inputs are resident in HBM when the timed region
+starts.  Prints one JSON line (rank 0).  The serving workload (--workload
+serving) replays the Poisson stream through the continuous-batching server.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium]
-                  [--precision mixed|fp64] [--impl lpk|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+                  [--workload assignment|tiny|medium|medium_0.1|serving]
+                  [--precision mixed|fp64] [--solver mrne|cgne|abgmres]
+                  [--impl lpk|reference]
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -25,21 +32,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "LPs solved/s & p99 latency at gap≤1e-8 (mixed vs FP64); NE-sweep HBM GB/s"
 UNIT = "LPs/s"
+SOLVERS = {"mrne": 0, "cgne": 1, "abgmres": 2}
 
-# workload -> (generator, options).  max_krylov 40000 is the relaxed Krylov cap
-# the paper uses for difficult problems (Sec. 4.2).
+# workload -> generator options and LPs per step.  max_krylov 40000 is the
+# relaxed Krylov cap the paper uses for difficult problems (Sec. 4.2).
 WORKLOADS = {
     "medium": dict(desc="rank-deficient sparse LP m=20000 n=60000, 8 nnz/col N(0,1), 1% dependent rows",
-                   opts=dict(solver=0, inner_sweeps=5, omega=1.0, max_krylov=40000)),
+                   opts=dict(solver=0, inner_sweeps=5, omega=1.0, max_krylov=40000), batch=1),
     "assignment": dict(desc="degenerate assignment LP k=14 (n=38416, m=588), costs U{0..100}",
-                       opts=dict(solver=0, inner_sweeps=3, omega=1.0)),
-    "tiny": dict(desc="tiny sparse LP m=50 n=120 ~5% N(0,1)", opts=dict(solver=0, inner_sweeps=1)),
+                       opts=dict(solver=2, inner_sweeps=3, omega=1.0), batch=16),
+    "tiny": dict(desc="tiny sparse LP m=50 n=120 ~5% N(0,1)", opts=dict(solver=0, inner_sweeps=1), batch=16),
     "medium_0.1": dict(desc="medium family at scale 0.1 (m=2000 n=6000)",
-                       opts=dict(solver=0, inner_sweeps=5, omega=1.0, max_krylov=6000)),
+                       opts=dict(solver=2, inner_sweeps=5, omega=1.0, max_krylov=6000), batch=8),
+    "serving": dict(desc="Poisson stream (rate 50/s) of LPs, m log-uniform in [100, 20000], n=3m, 6 nnz/col",
+                    opts=dict(solver=2, inner_sweeps=3, omega=1.0), batch=1),
 }
-
-
-SOLVERS = {"mrne": 0, "cgne": 1, "abgmres": 2}
 
 
 def make_lp(workload, seed_offset=0):
@@ -52,6 +59,8 @@ def make_lp(workload, seed_offset=0):
         return gen.assignment_lp(seed=gen.SEED_BASE + 3 + 1000 * seed_offset)
     if workload == "tiny":
         return gen.tiny_lp(seed=gen.SEED_BASE + 1 + 1000 * seed_offset)
+    if workload == "serving":
+        return gen.serving_lp(seed_offset)
     raise KeyError(workload)
 
 
@@ -133,71 +142,124 @@ def algorithmic_bytes(stats, m, n, nnz, precision):
             + stats.get("basis_passes", 0) * 8 * m)
 
 
+def percentile(vals, q):
+    v = sorted(vals)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
 def _oracle_kw(opts):
     return dict(method=opts.get("solver", 0), inner_sweeps=opts.get("inner_sweeps", 1),
                 omega=opts.get("omega", 1.0), max_krylov=opts.get("max_krylov", 0))
 
 
-def oracle_lp_seconds(lp, opts, krylov_iters_full, max_seconds=30.0):
-    """Seconds the oracle (single-threaded C) needs for one LP of the workload.
-    A first sample (starting point + first interior-point iteration, max_ipm=1)
-    gives its time per Krylov iteration; if the whole solve is estimated to
-    fit in max_seconds it is run and timed in full, else the estimate (time per
-    Krylov iteration x the Krylov iterations of the full solve) is returned."""
+def _oracle_worker(job):
+    """One LP of the workload solved by the oracle in a spawned process:
+    returns (seconds, ipm_iters, krylov_iters, status)."""
+    workload, seed_offset, opts, max_ipm = job
+    sys.path.insert(0, ROOT)
+    import oracle
+    lp = make_lp(workload, seed_offset)
+    kw = _oracle_kw(opts)
+    if max_ipm:
+        kw["max_ipm"] = max_ipm
+    t0 = time.perf_counter()
+    x, y, s, info = oracle.lp_solve_lp(lp, **kw)
+    return time.perf_counter() - t0, info["ipm_iters"], info["krylov_iters_total"], info["status_name"]
+
+
+def oracle_throughput(workload, opts, count, seed_base=0, pool=None, max_ipm=0):
+    """LPs/s of the oracle on min(count, host cores) processes, one LP per
+    process at a time; returns (LPs/s, cores, per-LP seconds, sample text)."""
     import oracle
     oracle.build()
-    kw = _oracle_kw(opts)
-    t0 = time.perf_counter()
-    x, y, s, info = oracle.lp_solve_lp(lp, max_ipm=1, **kw)
-    dt = time.perf_counter() - t0
-    its = max(1, int(info["krylov_iters_total"]))
-    est = dt / its * max(krylov_iters_full, its)
-    if est <= max_seconds:
+    cores = max(1, min(count, os.cpu_count() or 1))
+    jobs = [(workload, seed_base + i, opts, max_ipm) for i in range(count)]
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    try:
         t0 = time.perf_counter()
-        x, y, s, info = oracle.lp_solve_lp(lp, **kw)
-        full = time.perf_counter() - t0
-        return full, (f"one full oracle lp_solve of the same LP on 1 host thread: {full:.2f} s, "
-                      f"{info['ipm_iters']} IPM / {info['krylov_iters_total']} Krylov iterations, "
-                      f"status {info['status_name']}")
-    return est, (f"oracle lp_solve with max_ipm=1 (starting point + 1 IPM iteration, {its} Krylov "
-                 f"iterations in {dt:.2f} s on 1 host thread), scaled by the {krylov_iters_full} "
-                 f"Krylov iterations of the full solve: {est:.1f} s per LP")
+        res = pool.map(_oracle_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    per = [r[0] for r in res]
+    sample = (f"{count} LPs of the workload (seeds {seed_base}..{seed_base + count - 1}) solved by the oracle "
+              f"(single-threaded C, FP64), one LP per process on {cores} host cores in parallel: "
+              f"{wall:.1f} s wall, {statistics.mean(per):.2f} s per LP, status "
+              f"{sorted(set(r[3] for r in res))}")
+    if max_ipm:
+        sample += f", capped at {max_ipm} interior-point iterations per LP"
+    return count / wall, cores, per, sample
 
 
-def cpu_baseline(lp, opts, krylov_iters_full):
-    sec, sample = oracle_lp_seconds(lp, opts, krylov_iters_full)
-    return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds_per_lp": sec}
-
-
-def run_reference(args):
-    """--impl reference: the oracle on the host cores; each step is one LP of
-    the workload (a full oracle solve when it takes under 30 s, else the
-    bounded sample of oracle_lp_seconds)."""
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, wl, opts):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = WORKLOADS[args.workload]
-    lp = make_lp(args.workload)
-    opts = dict(wl["opts"])
-    if args.solver:
-        opts["solver"] = SOLVERS[args.solver]
-    secs, samples = [], []
-    for i in range(args.warmup + args.steps):
-        sec, sample = oracle_lp_seconds(lp, opts, args.ref_full_krylov)
-        if i >= args.warmup:
-            secs.append(sec)
-            samples.append(sample)
-    sec = statistics.mean(secs)
-    val = 1.0 / sec
+    B = args.batch if args.batch > 0 else wl["batch"]
+    # serving and medium LPs take the oracle minutes each: one interior-point
+    # iteration per LP bounds a step there (said in the sample text)
+    max_ipm = 1 if args.workload in ("serving", "medium") else 0
+    vals, samples = [], []
+    cores = 1
+    pool = mp.get_context("spawn").Pool(max(1, min(B, os.cpu_count() or 1)))
+    try:
+        for i in range(args.warmup + args.steps):
+            v, cores, per, sample = oracle_throughput(args.workload, opts, B, seed_base=0, pool=pool,
+                                                      max_ipm=max_ipm)
+            if i >= args.warmup:
+                vals.append(v)
+                samples.append(sample)
+    finally:
+        pool.close()
+        pool.join()
+    val = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl['desc']}", **{k: v for k, v in opts.items()}},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples[-1]},
+            "config": {"workload": f"{args.workload}: {wl['desc']}", "batch": B, **opts},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": samples[-1]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def sum_stats(ctxs):
+    tot = {}
+    for c in ctxs:
+        for k, v in c.stats().items():
+            if k in ("last_cluster_size", "last_resident"):
+                tot.setdefault(k, []).append(v)
+            else:
+                tot[k] = tot.get(k, 0) + v
+    return tot
+
+
+def roofline(stats, lp, precision, makespan_ms):
+    hbm, src = peaks()
+    launches = max(1, stats["krylov_launches"])
+    bytes_total = algorithmic_bytes(stats, lp.m, lp.n, lp.nnz, precision)
+    achieved = bytes_total / (stats["krylov_ms"] / 1e3) / 1e9 if stats["krylov_ms"] > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "k_krylov (persistent search-direction solve)",
+            "peak_source": f"{src} hbm_gbs", "avg_launch_ms": stats["krylov_ms"] / launches,
+            "launches": stats["krylov_launches"], "bytes_per_launch": bytes_total / launches,
+            "barriers_per_launch": stats["barriers"] / launches,
+            "us_per_barrier_phase": 1e3 * stats["krylov_ms"] / max(1, stats["barriers"]),
+            "aggregate_gbs": bytes_total / (makespan_ms / 1e3) / 1e9 if makespan_ms > 0 else None}
 
 
 def main():
@@ -206,26 +268,25 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lpk", choices=["lpk", "reference"])
-    # default: the assignment LP; a medium LP solve takes minutes with the
-    # current kernels (several hundred thousand Krylov iterations), too long
-    # for a default run with three warm-up solves
     ap.add_argument("--workload", default="assignment", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="LPs per step solved side by side (0: workload's)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--solver", default="", choices=["", "mrne", "cgne", "abgmres"],
+    ap.add_argument("--solver", default="", choices=[""] + sorted(SOLVERS),
                     help="Krylov solver (default: the workload's)")
-    ap.add_argument("--compare-fp64", type=int, default=1, help="also time K FP64 solves")
+    ap.add_argument("--compare-fp64", type=int, default=3,
+                    help="FP64 LPs timed one at a time on the single-LP path (0: skip)")
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--cpu-baseline", type=int, default=1)
-    ap.add_argument("--ref-full-krylov", type=int, default=0,
-                    help="reference arm: Krylov iterations of a full solve (0: measured by one GPU solve)")
+    ap.add_argument("--serving-count", type=int, default=48, help="serving: LPs of the stream replayed")
+    ap.add_argument("--lanes", type=int, default=16, help="serving: server lanes")
     args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    opts = dict(wl["opts"])
+    if args.solver:
+        opts["solver"] = SOLVERS[args.solver]
     if args.impl == "reference":
-        if args.ref_full_krylov <= 0:
-            args.ref_full_krylov = {"medium": 700000, "medium_0.1": 69305, "assignment": 9333,
-                                    "tiny": 515}[args.workload]
-        return run_reference(args)
+        return run_reference(args, wl, opts)
 
-    import numpy as np
     import torch
 
     rank = int(os.environ.get("RANK", "0"))
@@ -243,132 +304,205 @@ def main():
     __graft_entry__.build()
     from paper_1604_07491_gb300 import lpk
 
-    wl = WORKLOADS[args.workload]
-    opts = dict(wl["opts"])
-    if args.solver:
-        opts["solver"] = SOLVERS[args.solver]
-    prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
-    # replicas: each rank solves its own LP of the same family (weak scaling)
-    lp = make_lp(args.workload, seed_offset=rank)
-    stream = torch.cuda.current_stream(dev)
-    ctx = lpk.Context(local, stream.cuda_stream)
-    P = lpk.Problem.from_lp(ctx, lp, device=dev)
-    b = torch.from_numpy(lp.b).to(dev)
-    c = torch.from_numpy(lp.c).to(dev)
-    out = (torch.empty(lp.n, dtype=torch.float64, device=dev), torch.empty(lp.m, dtype=torch.float64, device=dev),
-           torch.empty(lp.n, dtype=torch.float64, device=dev))
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def solve(p):
-        return P.lp_solve(b, c, out=out, precision=p, **opts)
+    if args.workload == "serving":
+        line = run_serving(args, wl, opts, lpk, local, rank, world, barrier)
+    else:
+        line = run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
-    infos = []
+
+def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist):
+    import numpy as np
+    B = args.batch if args.batch > 0 else wl["batch"]
+    prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
+    # replicas: rank r solves its own LPs of the same family (weak scaling)
+    lps = [make_lp(args.workload, seed_offset=rank * B + i) for i in range(B)]
+    main_stream = torch.cuda.current_stream(dev)
+    streams = [main_stream] if B == 1 else [torch.cuda.Stream(dev) for _ in range(B)]
+    ctxs = [lpk.Context(local, st.cuda_stream) for st in streams]
+    probs = [lpk.Problem.from_lp(ctxs[i], lps[i], device=dev) for i in range(B)]
+    bs = [torch.from_numpy(lp.b).to(dev) for lp in lps]
+    cs = [torch.from_numpy(lp.c).to(dev) for lp in lps]
+    outs = [(torch.empty(lp.n, dtype=torch.float64, device=dev), torch.empty(lp.m, dtype=torch.float64, device=dev),
+             torch.empty(lp.n, dtype=torch.float64, device=dev)) for lp in lps]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    torch.cuda.synchronize(dev)
+
+    def step(p):
+        if B == 1:
+            return [probs[0].lp_solve(bs[0], cs[0], out=outs[0], precision=p, **opts)]
+        return lpk.solve_batch(probs, bs, cs, outs=outs, precision=p, **opts)
+
     for _ in range(args.warmup):
-        infos.append(solve(prec)[3])
-    ctx.reset_stats()
-    step_ms = []
+        step(prec)
+    for c in ctxs:
+        c.reset_stats()
+    step_ms, lat_ms, infos = [], [], []
     with ClockSampler(local) as clk:
         for _ in range(args.steps):
             flush.zero_()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x, y, s, info = solve(prec)
-            e1.record(stream)
+            e0.record(main_stream)
+            res = step(prec)
+            e1.record(main_stream)
             barrier()
             step_ms.append(e0.elapsed_time(e1))
-            infos.append(info)
-    stats = ctx.stats()
+            for r in res:
+                lat_ms.append(r[3]["solve_ms"])
+                infos.append(r[3])
+    stats = sum_stats(ctxs)
     total_ms = sum(step_ms)
     tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if dist is not None:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     total_ms = float(tmax.item())
-    lps = world * args.steps / (total_ms / 1e3)
-    last = infos[-1]
+    lps_per_s = world * B * args.steps / (total_ms / 1e3)
+    worst = max(infos, key=lambda d: (d["status"] != 0, d["rel_gap"]))
 
-    # FP64 comparison on the same LP (same steps)
+    # plain FP64, one LP at a time, on the autotuned single-LP path
     fp64 = None
-    if args.compare_fp64 and prec == lpk.MIXED:
-        solve(lpk.FP64)  # warm the FP64 kernels
-        ms64 = []
-        for _ in range(args.steps):
+    if args.compare_fp64 > 0:
+        ctx1 = lpk.Context(local, main_stream.cuda_stream)
+        k = min(args.compare_fp64, B)
+        p1 = [lpk.Problem.from_lp(ctx1, lps[i], device=dev) for i in range(k)]
+        p1[0].lp_solve(bs[0], cs[0], out=outs[0], precision=lpk.FP64, **opts)  # warm-up (and autotune)
+        ms64, inf64 = [], []
+        for i in range(k):
             flush.zero_()
             barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r64 = solve(lpk.FP64)[3]
-            e1.record(stream)
+            e0.record(main_stream)
+            r = p1[i].lp_solve(bs[i], cs[i], out=outs[i], precision=lpk.FP64, **opts)[3]
+            e1.record(main_stream)
             barrier()
             ms64.append(e0.elapsed_time(e1))
-        fp64 = {"value": world * args.steps / (sum(ms64) / 1e3), "unit": UNIT,
-                "ms_per_step": statistics.mean(ms64), "status": r64["status_name"],
-                "ipm_iters": r64["ipm_iters"], "krylov_iters": r64["krylov_iters_total"],
-                "obj": r64["obj_primal"]}
+            inf64.append(r)
+        fp64 = {"value": world * k / (sum(ms64) / 1e3), "unit": UNIT, "mode": "FP64, one LP at a time",
+                "ms_per_lp": statistics.mean(ms64), "lps": k,
+                "status": sorted({d["status_name"] for d in inf64}),
+                "max_rel_gap": max(d["rel_gap"] for d in inf64), "max_pinf": max(d["pinf"] for d in inf64),
+                "max_dinf": max(d["dinf"] for d in inf64),
+                "obj_rel_diff_vs_batch": max(abs(inf64[i]["obj_primal"] - infos[i]["obj_primal"])
+                                             / max(1.0, abs(inf64[i]["obj_primal"])) for i in range(k))}
+        for p in p1:
+            p.free()
+        ctx1.close()
 
-    # end to end through the C ABI with host buffers: prepare from host CSR,
-    # H2D of A, b, c and D2H of x, y, s inside the timed region
+    # end to end through the C ABI with host buffers: prepare from host CSR
+    # (H2D of A inside), b, c from host, x, y, s back to host, all timed
     e2e = None
     if args.e2e:
-        h_out = (np.empty(lp.n), np.empty(lp.m), np.empty(lp.n))
+        h_out = [(np.empty(lp.n), np.empty(lp.m), np.empty(lp.n)) for lp in lps]
         barrier()
         t0 = time.perf_counter()
-        Ph = lpk.Problem.from_lp(ctx, lp)
-        r = Ph.lp_solve(lp.b, lp.c, out=h_out, precision=prec, **opts)
-        Ph.free()
+        ph = [lpk.Problem.from_lp(ctxs[i], lps[i]) for i in range(B)]
+        if B == 1:
+            r = [ph[0].lp_solve(lps[0].b, lps[0].c, out=h_out[0], precision=prec, **opts)]
+        else:
+            r = lpk.solve_batch(ph, [lp.b for lp in lps], [lp.c for lp in lps], outs=h_out, precision=prec,
+                                **opts)
+        for p in ph:
+            p.free()
         t1 = time.perf_counter()
-        h2d = lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.val.nbytes + lp.b.nbytes + lp.c.nbytes
-        d2h = sum(a.nbytes for a in h_out)
-        e2e = {"value": world / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "status": r[3]["status_name"]}
+        h2d = sum(lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.val.nbytes + lp.b.nbytes + lp.c.nbytes for lp in lps)
+        d2h = sum(a.nbytes for t in h_out for a in t)
+        e2e = {"value": world * B / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "status": sorted({x[3]["status_name"] for x in r})}
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return
-
-    hbm, src = peaks()
-    kernel_ms = stats["krylov_ms"] / max(1, stats["krylov_launches"])
-    bytes_total = algorithmic_bytes(stats, lp.m, lp.n, lp.nnz, args.precision)
-    achieved = bytes_total / (stats["krylov_ms"] / 1e3) / 1e9 if stats["krylov_ms"] > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_krylov (persistent search-direction solve)",
-                "peak_source": f"{src} hbm_gbs", "avg_launch_ms": kernel_ms,
-                "launches": stats["krylov_launches"], "bytes_per_launch": bytes_total / max(1, stats["krylov_launches"]),
-                "barriers_per_launch": stats["barriers"] / max(1, stats["krylov_launches"]),
-                "us_per_barrier_phase": 1e3 * stats["krylov_ms"] / max(1, stats["barriers"])}
+        return None
     cpu = None
     if args.cpu_baseline and world == 1:
-        cpu = cpu_baseline(lp, opts, int(last["krylov_iters_total"]))
-    lat = sorted(step_ms)
-    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
-    line = {
-        "metric": METRIC, "value": lps, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        v, cores, per, sample = oracle_throughput(args.workload, opts, min(B, os.cpu_count() or 1))
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds_per_lp": statistics.mean(per)}
+    lp0 = lps[0]
+    return {
+        "metric": METRIC, "value": lps_per_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 values / f64 accumulation" if prec == lpk.MIXED else "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {wl['desc']}", "m": lp.m, "n": lp.n, "nnz": lp.nnz,
-                   "n_colors": P.n_colors, "precision": args.precision,
-                   "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]], "inner_sweeps": opts["inner_sweeps"],
-                   "omega": opts.get("omega", 1.0), "max_krylov": opts.get("max_krylov", 0),
+        "config": {"workload": f"{args.workload}: {wl['desc']}", "m": lp0.m, "n": lp0.n, "nnz": lp0.nnz,
+                   "n_colors": probs[0].n_colors, "batch": B, "global_batch": B * world,
+                   "precision": args.precision, "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]],
+                   "inner_sweeps": opts["inner_sweeps"], "omega": opts.get("omega", 1.0),
+                   "max_krylov": opts.get("max_krylov", 0),
+                   "exec": "batch path: one context, stream and thread-block cluster per LP" if B > 1
+                   else "single-LP path (autotuned)",
+                   "cluster_sizes": sorted(set(stats.get("last_cluster_size", []))),
                    "parallelism": f"replicas x{world}", "l2": "256 MB buffer written between timed steps",
                    "inputs": "resident in HBM (prepare outside the timed region)"},
-        "p50_ms": statistics.median(step_ms), "p99_ms": p99,
-        "solve": {"status": last["status_name"], "ipm_iters": last["ipm_iters"],
-                  "krylov_iters": last["krylov_iters_total"], "obj": last["obj_primal"],
-                  "gamma": last["gamma"], "rel_gap": last["rel_gap"], "pinf": last["pinf"], "dinf": last["dinf"]},
-        "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": stats["launches"], "clocks": clk.summary(),
+        "p50_ms": percentile(lat_ms, 0.50), "p99_ms": percentile(lat_ms, 0.99),
+        "latency": "per-LP solve time (CUDA events on the LP's stream) within its batch",
+        "solve": {"status": sorted({d["status_name"] for d in infos}), "ipm_iters": worst["ipm_iters"],
+                  "krylov_iters_mean": statistics.mean(d["krylov_iters_total"] for d in infos),
+                  "max_rel_gap": max(d["rel_gap"] for d in infos), "max_pinf": max(d["pinf"] for d in infos),
+                  "max_dinf": max(d["dinf"] for d in infos)},
+        "fp64": fp64, "roofline": roofline(stats, lp0, args.precision, total_ms),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": stats["launches"], "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+
+
+def run_serving(args, wl, opts, lpk, local, rank, world, barrier):
+    """Replay the first N LPs of the Poisson stream through the server: each is
+    submitted at its arrival time; latency = result ready - arrival."""
+    from paper_1604_07491_gb300 import gen
+    N = args.serving_count
+    arrivals = gen.serving_arrivals(N)
+    lps = [make_lp("serving", seed_offset=rank * N + i) for i in range(N)]
+    prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
+    srv = lpk.Server(local, lanes=args.lanes)
+    # warm-up: a few small LPs (kernel loading, pool growth)
+    for t in [srv.submit_lp(make_lp("tiny", i), precision=prec, **WORKLOADS["tiny"]["opts"]) for i in range(3)]:
+        srv.wait(t)
+    barrier()
+    tickets = []
+    with ClockSampler(local) as clk:
+        t0 = srv.now()
+        for i, lp in enumerate(lps):
+            delay = t0 + arrivals[i] - srv.now()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit_lp(lp, precision=prec, **opts))
+        res = [srv.wait(t) for t in tickets]
+        barrier()
+    st = srv.stats()
+    srv.close()
+    lat = [1e3 * (r[3]["t_end"] - r[3]["t_submit"]) for r in res]
+    span = max(r[3]["t_end"] for r in res) - min(r[3]["t_submit"] for r in res)
+    infos = [r[3]["info"] for r in res]
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": world * N / span, "unit": UNIT, "n_gpus": world, "steps": 1,
+        "warmup": 3, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 values / f64 accumulation" if prec == lpk.MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"serving: {wl['desc']}", "lps": N, "lanes": args.lanes,
+                   "m_range": [min(lp.m for lp in lps), max(lp.m for lp in lps)], "precision": args.precision,
+                   "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]], "inner_sweeps": opts["inner_sweeps"],
+                   "l2": "inputs of every LP differ (no reuse)", "inputs": "host CSR submitted at arrival"},
+        "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+        "latency": "arrival to result (queueing + prepare + solve + copy-out)",
+        "solve": {"status": sorted({d["status_name"] for d in infos}),
+                  "max_rel_gap": max(d["rel_gap"] for d in infos)},
+        "server": st, "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": world * N / span, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(lp.row_ptr.nbytes + lp.col_idx.nbytes + lp.val.nbytes
+                                              + lp.b.nbytes + lp.c.nbytes for lp in lps)),
+                "d2h_bytes_per_step": int(sum(8 * (2 * lp.n + lp.m) for lp in lps))},
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
 
 
 if __name__ == "__main__":

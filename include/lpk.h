@@ -159,6 +159,14 @@ typedef struct lpk_stats {
  *  LPK_EXEC_GRID:    every SM, software grid barrier, u in global memory.
  *  LPK_EXEC_CLUSTER: the cluster path (LPK_INVALID_ARG at solve time if u does
  *                    not fit).
+ *  LPK_EXEC_BATCH:   the cluster path with a cluster size fixed by the problem
+ *                    alone (no timing): the smallest of 4, 8, 16 CTAs that
+ *                    gives every warp at most three rows per color and keeps
+ *                    the rows resident.  For solves that share the GPU
+ *                    (batched and serving modes): small clusters leave room
+ *                    for many problems at once, and a problem gives bitwise
+ *                    the same result alone and among others.  LPK_INVALID_ARG
+ *                    at solve time if u does not fit in 16 CTAs.
  * Or-ing LPK_EXEC_NO_RESIDENT disables the shared-memory row cache (by
  * default each warp keeps the column indices and values of its rows in shared
  * memory for the whole launch when they fit).
@@ -167,6 +175,7 @@ typedef enum lpk_exec {
   LPK_EXEC_AUTO = 0,
   LPK_EXEC_GRID = 1,
   LPK_EXEC_CLUSTER = 2,
+  LPK_EXEC_BATCH = 3,
   LPK_EXEC_NO_RESIDENT = 4
 } lpk_exec;
 
@@ -270,5 +279,85 @@ LPK_API lpk_status lpk_ne_solve_noalloc(lpk_ctx *ctx, lpk_problem *P, const doub
 LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, const double *c,
                                 const lpk_options *opt, double *x, double *y, double *s,
                                 lpk_info *info, int32_t on_device);
+
+/* ------------------------------------------------------------------------
+ * Many LPs on one GPU (the paper solves one LP at a time and has no
+ * counterpart).  Independent LPs run side by side, each on its own context
+ * (one host thread and CUDA stream per LP) with its persistent Krylov kernel
+ * on a thread-block cluster of its own; contexts in LPK_EXEC_AUTO mode take
+ * the LPK_EXEC_BATCH path for these solves, so every LP gives bitwise the
+ * result it gives when solved alone on that path.
+ * ------------------------------------------------------------------------ */
+
+/* Solve `count` LPs at once: LP i is problems[i] with b[i], c[i] (lengths as
+ * for lpk_lp_solve), results into x[i], y[i], s[i] and info[i].  Each problem
+ * must belong to a different context, and no context may be set to
+ * LPK_EXEC_GRID (its barrier spans every SM, so it cannot share the GPU):
+ * LPK_INVALID_ARG otherwise, before anything runs (the message is on the
+ * offending context).  `opt` (NULL: defaults) applies to all.  Returns LPK_OK
+ * if every solve returned LPK_OK, else the status of the first LP (by index)
+ * that did not; info[i].status holds each LP's own status.  Blocks until all
+ * are done. */
+LPK_API lpk_status lpk_lp_solve_batch(int32_t count, lpk_problem *const *problems, const double *const *b,
+                                      const double *const *c, const lpk_options *opt, double *const *x,
+                                      double *const *y, double *const *s, lpk_info *info,
+                                      int32_t on_device);
+
+/* Continuous-batching server.  `lanes` worker threads, each with its own
+ * context and non-blocking stream on `device`, take submitted LPs in arrival
+ * order as soon as a lane is free and the LP's device memory estimate (the
+ * prepared problem, the interior-point and Krylov workspaces and, for
+ * AB-GMRES, its basis sized to the iteration cap) fits in what the running
+ * LPs leave of `mem_budget` (0: half the free device memory at creation); an
+ * LP that does not fit waits while later, smaller ones may start, and the
+ * oldest waiting LP starts whenever nothing runs, even if it alone exceeds
+ * the budget.  Each LP's matrix, iterate and Krylov state stay on the device
+ * from admission to its result. */
+typedef struct lpk_server lpk_server;
+typedef struct lpk_server_config {
+  int32_t device;
+  int32_t lanes;        /* 1..256, default 16 */
+  int64_t mem_budget;   /* bytes; 0 = half the free device memory */
+  uint64_t color_seed;  /* coloring seed of every LP (as lpk_prepare) */
+} lpk_server_config;
+/* Per-LP outcome.  Times are seconds on the server's steady clock
+ * (lpk_server_now): submission, admission to a lane, result ready. */
+typedef struct lpk_request_result {
+  lpk_info info;
+  int32_t status;       /* lpk_prepare / lpk_lp_solve status */
+  int32_t lane;
+  double t_submit, t_start, t_end;
+  int64_t mem_bytes;    /* device memory charged at admission */
+  char error[256];      /* lpk_last_error text when status != LPK_OK */
+} lpk_request_result;
+typedef struct lpk_server_stats_t {
+  int64_t pending, running, completed;
+  int64_t mem_in_use, mem_peak, mem_budget;
+  int32_t lanes, reserved;
+} lpk_server_stats_t;
+
+LPK_API void lpk_server_default_config(lpk_server_config *cfg);
+/* cfg NULL: defaults.  LPK_CUDA_ERROR if a lane's stream or context cannot
+ * be created. */
+LPK_API lpk_status lpk_server_create(lpk_server **srv, const lpk_server_config *cfg);
+/* Stops taking LPs, drops the ones not yet admitted, waits for the running
+ * ones and releases everything.  No other call on srv may run concurrently
+ * or follow. */
+LPK_API void lpk_server_destroy(lpk_server *srv);
+LPK_API double lpk_server_now(const lpk_server *srv);
+/* Queue one LP (A in host CSR, A->on_device must be 0; b[m], c[n] host).
+ * Everything is copied: the caller's arrays may be reused on return.  Options
+ * as lpk_lp_solve (NULL: defaults).  Returns a ticket for lpk_server_wait.
+ * Thread-safe. */
+LPK_API lpk_status lpk_server_submit(lpk_server *srv, const lpk_matrix *A, const double *b, const double *c,
+                                     const lpk_options *opt, int64_t *ticket);
+/* Wait up to timeout_s seconds (< 0: no limit) for a ticket's result; copies
+ * x[n], y[m], s[n] (each may be NULL) and the outcome, then releases the
+ * ticket.  LPK_TIMEOUT if not ready (the ticket stays valid);
+ * LPK_INVALID_ARG for an unknown ticket.  The LP's own status is in
+ * res->status.  Thread-safe. */
+LPK_API lpk_status lpk_server_wait(lpk_server *srv, int64_t ticket, double timeout_s, double *x, double *y,
+                                   double *s, lpk_request_result *res);
+LPK_API lpk_status lpk_server_stats(lpk_server *srv, lpk_server_stats_t *out);
 
 #endif /* LPK_H */

@@ -29,7 +29,7 @@ struct Vec {
   }
   lpk_status init() {
     if (!owned) return LPK_OK;
-    LPK_CUDA_TRY(ctx, cudaMalloc(&dev, sizeof(double) * (len > 0 ? len : 1)));
+    LPK_CUDA_TRY(ctx, dev_alloc(ctx, &dev, len));
     if (!out && len)
       LPK_CUDA_TRY(ctx, cudaMemcpyAsync(dev, user, sizeof(double) * len, cudaMemcpyHostToDevice, ctx->stream));
     return LPK_OK;
@@ -41,17 +41,17 @@ struct Vec {
   }
   ~Vec() {
     if (owned && dev) {
-      cudaStreamSynchronize(ctx->stream);
-      cudaFree(dev);
+      dev_free(ctx->stream, dev);
+      cudaStreamSynchronize(ctx->stream);  // outputs are in the caller's host buffer on return
     }
   }
 };
 
-struct DevBuf {
+struct DevBuf {  // temporary device vector of one call (stream-ordered free)
+  lpk_ctx *ctx;
   double *p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
+  explicit DevBuf(lpk_ctx *c) : ctx(c) {}
+  ~DevBuf() { dev_free(ctx->stream, p); }
 };
 
 __global__ void k_ahat_to_input(long long nnz, const long long *src, const double *ah, double *out) {
@@ -83,13 +83,13 @@ __global__ void k_d2_check(int n, const double *d2, int *bad) {
 
 lpk_status check_d2(lpk_ctx *ctx, const DevProblem &P, const double *d2_int) {
   int *bad;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&bad, sizeof(int)));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &bad, 1));
   cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream);
   if (P.n > 0) LPK_LAUNCH(ctx, k_d2_check, (P.n + 255) / 256, 256, 0, ctx->stream, P.n, d2_int, bad);
   int h = 0;
   cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  dev_free(ctx->stream, bad);
   cudaStreamSynchronize(ctx->stream);
-  cudaFree(bad);
   if (h) {
     ctx->err = "d2 must be positive and finite";
     return LPK_INVALID_ARG;
@@ -126,13 +126,14 @@ LPK_API void lpk_destroy(lpk_ctx *ctx) {
     p->ctx = nullptr;
   }
   ctx->problems.clear();
-  if (ctx->red_part) cudaFree(ctx->red_part);
-  if (ctx->red_count) cudaFree(ctx->red_count);
-  if (ctx->red_out) cudaFree(ctx->red_out);
+  dev_free(ctx->stream, ctx->red_part);
+  dev_free(ctx->stream, ctx->red_count);
+  dev_free(ctx->stream, ctx->red_out);
+  dev_free(ctx->stream, ctx->kctl);
+  dev_free(ctx->stream, ctx->kpart);
+  cudaStreamSynchronize(ctx->stream);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
-  if (ctx->kctl) cudaFree(ctx->kctl);
   if (ctx->h_kctl) cudaFreeHost(ctx->h_kctl);
-  if (ctx->kpart) cudaFree(ctx->kpart);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
@@ -150,9 +151,9 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
   if (!ctx) return LPK_INVALID_ARG;
   const int no_res = (exec & LPK_EXEC_NO_RESIDENT) != 0;
   exec &= ~LPK_EXEC_NO_RESIDENT;
-  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_CLUSTER ||
+  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_BATCH ||
       !(cluster_size == 0 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8 || cluster_size == 16)) {
-    ctx->err = "lpk_set_exec: exec must be 0..2 and cluster_size 0, 2, 4, 8 or 16";
+    ctx->err = "lpk_set_exec: exec must be 0..3 and cluster_size 0, 2, 4, 8 or 16";
     return LPK_INVALID_ARG;
   }
   ctx->cluster_mode = exec;
@@ -265,8 +266,8 @@ LPK_API lpk_status lpk_scale_rows(lpk_ctx *ctx, lpk_problem *P, const double *d2
   TRY(vd2.init());
   TRY(vrho.init());
   TRY(vah.init());
-  DevBuf t;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&t.p, sizeof(double) * (d.n + 1)));
+  DevBuf t(ctx);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &t.p, d.n + 1));
   gather_n(ctx, d, vd2.dev, t.p);
   TRY(check_d2(ctx, d, t.p));
   scale_rows(ctx, d, t.p);
@@ -290,8 +291,8 @@ LPK_API lpk_status lpk_spmv(lpk_ctx *ctx, lpk_problem *P, int32_t transpose, con
   Vec vx(ctx, x, lx, on_device, false), vy(ctx, y, ly, on_device, true);
   TRY(vx.init());
   TRY(vy.init());
-  DevBuf a, b;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&a.p, sizeof(double) * (d.m + d.n + 2)));
+  DevBuf a(ctx), b(ctx);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &a.p, d.m + d.n + 2));
   b.p = nullptr;
   double *tm = a.p, *tn = a.p + d.m + 1;
   if (transpose) {
@@ -326,8 +327,8 @@ LPK_API lpk_status lpk_sweep(lpk_ctx *ctx, lpk_problem *P, const double *d2, con
   TRY(vg.init());
   TRY(vz.init());
   TRY(vu.init());
-  DevBuf t;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&t.p, sizeof(double) * (2 * d.m + 2 * d.n + 4)));
+  DevBuf t(ctx);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &t.p, 2 * d.m + 2 * d.n + 4));
   double *td2 = t.p, *tg = td2 + d.n + 1, *tz = tg + d.m + 1, *tu = tz + d.m + 1;
   gather_n(ctx, d, vd2.dev, td2);
   TRY(check_d2(ctx, d, td2));
@@ -362,8 +363,8 @@ LPK_API lpk_status lpk_ne_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, 
   TRY(vf.init());
   TRY(vdy.init());
   TRY(vdw.init());
-  DevBuf t;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&t.p, sizeof(double) * (3 * d.m + 2 * d.n + 5)));
+  DevBuf t(ctx);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &t.p, 3 * d.m + 2 * d.n + 5));
   double *td2 = t.p, *tf = td2 + d.n + 1, *tdy = tf + d.m + 1, *tdw = tdy + d.m + 1, *tmp = tdw + d.n + 1;
   gather_n(ctx, d, vd2.dev, td2);
   TRY(check_d2(ctx, d, td2));

@@ -253,10 +253,21 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
   info = lpk_info{};
   info.n_colors = P.n_colors;
 
+  // workspace (kept with the problem): 10 m-vectors, 17 n-vectors, flags
+  const size_t mm = m > 0 ? m : 1, nn = n > 0 ? n : 1;
+  const size_t need = sizeof(double) * (10 * mm + 17 * nn + 4);
+  if (P.ipm_bytes < need) {
+    dev_free(st, P.ipm_buf);
+    P.ipm_buf = nullptr;
+    P.ipm_bytes = 0;
+    LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ipm_buf, need / sizeof(double)));
+    P.ipm_bytes = need;
+  }
+  double *buf = P.ipm_buf;
+
   // checks on b and c (input numbering)
   {
-    int *flags;
-    LPK_CUDA_TRY(ctx, cudaMalloc(&flags, sizeof(int)));
+    int *flags = (int *)(buf + 10 * mm + 17 * nn);
     LPK_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int), st));
     int len = std::max(P.m_in, P.n_in);
     if (len > 0)
@@ -264,7 +275,6 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
     int hf = 0;
     cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    cudaFree(flags);
     if (hf & 4) {
       ctx->err = "b or c has a non-finite entry";
       info.status = LPK_INVALID_ARG;
@@ -282,11 +292,6 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
     }
   }
 
-  // workspace: 10 m-vectors, 17 n-vectors
-  const size_t mm = m > 0 ? m : 1, nn = n > 0 ? n : 1;
-  double *buf;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&buf, sizeof(double) * (10 * mm + 17 * nn)));
-  struct Free { double *p; ~Free() { cudaFree(p); } } freer{buf};
   double *q = buf;
   auto take_m = [&]() { double *r = q; q += mm; return r; };
   auto take_n = [&]() { double *r = q; q += nn; return r; };

@@ -133,10 +133,10 @@ void scatter_n(lpk_ctx *ctx, const DevProblem &P, const double *in, double *out,
 lpk_status ensure_reduce(lpk_ctx *ctx) {
   if (ctx->red_part) return LPK_OK;
   ctx->red_blocks = 2 * ctx->num_sms;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->red_part, sizeof(double) * RED_MAX_SLOTS * ctx->red_blocks));
-  LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->red_count, sizeof(unsigned)));
-  LPK_CUDA_TRY(ctx, cudaMemset(ctx->red_count, 0, sizeof(unsigned)));
-  LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->red_out, sizeof(double) * RED_MAX_SLOTS));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &ctx->red_part, (size_t)RED_MAX_SLOTS * ctx->red_blocks));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &ctx->red_count, 1));
+  LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->red_count, 0, sizeof(unsigned), ctx->stream));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &ctx->red_out, RED_MAX_SLOTS));
   LPK_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_red, sizeof(double) * RED_MAX_SLOTS));
   return LPK_OK;
 }

@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "lpk_internal.cuh"
@@ -1117,10 +1118,10 @@ lpk_status get_ws(lpk_ctx *ctx, DevProblem &P, Workspace &W) {
   const size_t m = P.m > 0 ? P.m : 1, n = P.n > 0 ? P.n : 1;
   const size_t need = sizeof(double) * (6 * m + 6 * n) + 4096;
   if (P.ws_bytes < need) {
-    if (P.ws) cudaFree(P.ws);
+    dev_free(P.stream, P.ws);
     P.ws = nullptr;
     P.ws_bytes = 0;
-    LPK_CUDA_TRY(ctx, cudaMalloc(&P.ws, need));
+    LPK_CUDA_TRY(ctx, dev_alloc_bytes(ctx, &P.ws, need));
     P.ws_bytes = need;
   }
   double *b = (double *)P.ws;
@@ -1169,11 +1170,11 @@ lpk_status get_gmres(lpk_ctx *ctx, DevProblem &P, int maxit, KArgs &A) {
   }
   const size_t need = gm_doubles(m, kmax, S, &ld);
   if (P.gm_kmax < kmax || P.gm_m != m) {
-    if (P.gm_V) cudaFree(P.gm_V);
+    dev_free(P.stream, P.gm_V);
     P.gm_V = nullptr;
     P.gm_bytes = 0;
     P.gm_kmax = 0;
-    LPK_CUDA_TRY(ctx, cudaMalloc(&P.gm_V, need * sizeof(double)));
+    LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.gm_V, need));
     P.gm_bytes = need * sizeof(double);
     P.gm_kmax = kmax;
     P.gm_m = m;
@@ -1199,9 +1200,9 @@ lpk_status get_gmres(lpk_ctx *ctx, DevProblem &P, int maxit, KArgs &A) {
 
 lpk_status ensure_kctl(lpk_ctx *ctx) {
   if (ctx->kctl) return LPK_OK;
-  LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->kctl, sizeof(KrylovCtl)));
+  LPK_CUDA_TRY(ctx, dev_alloc_bytes(ctx, &ctx->kctl, sizeof(KrylovCtl)));
   LPK_CUDA_TRY(ctx, cudaMallocHost(&ctx->h_kctl, sizeof(KrylovCtl)));
-  LPK_CUDA_TRY(ctx, cudaMalloc(&ctx->kpart, sizeof(double) * 8 * 4096));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &ctx->kpart, 8 * 4096));
   return LPK_OK;
 }
 
@@ -1216,6 +1217,25 @@ void *kernel_for(int method, int f32) {
 // dynamic shared memory per CTA: the opt-in maximum (227 KB) minus room for
 // the kernels' static shared memory
 constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;
+
+// Function attributes of a kernel variant, set once per process: the largest
+// dynamic shared memory any launch may request and non-portable cluster sizes.
+// Setting them per launch (to the launch's own size) would race between
+// contexts that launch from different host threads.
+std::mutex g_attr_mu;
+std::vector<const void *> g_attr_done;
+
+cudaError_t prepare_fn(const void *fn) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (const void *f : g_attr_done)
+    if (f == fn) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_LIMIT);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  g_attr_done.push_back(fn);
+  return cudaSuccess;
+}
 
 // Shared-memory layout of one CTA: [u slice (cluster path)] [z slots]
 // [row descriptors] [row indices] [color offsets] and, when the rows are
@@ -1295,10 +1315,46 @@ void exec_mode(lpk_ctx *ctx, const DevProblem &P, int *mode, int *csov) {
   }
 }
 
-int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int *shift) {
+// u slice (2^s doubles per CTA) for a cluster of cs CTAs, or -1 if too large
+int u_shift_for(const DevProblem &P, int cs) {
+  int s = 5;
+  while ((1ll << s) * cs < P.n) ++s;
+  return s > MAX_SHIFT ? -1 : s;
+}
+
+// Batched mode: a cluster size fixed by the problem alone (no timing), so a
+// problem runs the same reductions alone and among others.  The smallest of
+// 4, 8 and 16 CTAs that gives each warp at most three rows per color on
+// average and keeps every warp's rows resident in shared memory; failing
+// that, the smallest with room for u.  Small clusters leave room for many
+// problems at once.  Returns 0 if u does not fit in 16 CTAs.
+int batch_cluster(const DevProblem &P, int f32, bool allow_resident) {
+  const long long per_color = P.n_colors > 0 ? (P.m + P.n_colors - 1) / P.n_colors : P.m;
+  int cs0 = 4;
+  while (cs0 < MAX_CLUSTER && (long long)cs0 * KWPB * 3 < per_color) cs0 *= 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int cs = cs0; cs <= MAX_CLUSTER; cs *= 2) {
+      const int s = u_shift_for(P, cs);
+      if (s < 0) continue;
+      const SmemPlan L = plan_smem(P, cs, sizeof(double) << s, f32 ? 4 : 8, allow_resident && pass == 0);
+      if (L.total > SMEM_LIMIT || (pass == 0 && !L.resident)) continue;
+      return cs;
+    }
+  }
+  return 0;
+}
+
+int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int f32, int *shift) {
   int mode, csov;
   exec_mode(ctx, P, &mode, &csov);
   if (mode == 1 || P.n <= 0) return 0;  // grid
+  if (mode == 3) {
+    const int cs = csov > 0 ? csov : batch_cluster(P, f32, ctx->resident_mode == 0);
+    const int s = cs > 0 ? u_shift_for(P, cs) : -1;
+    if (s < 0) return -1;
+    *shift = s;
+    return cs;
+  }
   int cs = 2;
   while (cs < MAX_CLUSTER && (long long)cs * 16384 < P.nnz) cs *= 2;
   if (csov > 0) cs = csov;
@@ -1318,7 +1374,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
   }
   int shift = 0;
-  const int cs = cluster_plan(ctx, P, &shift);
+  const int cs = cluster_plan(ctx, P, f32, &shift);
   if (cs < 0) {
     ctx->err = "cluster path requested but u does not fit in one cluster's shared memory";
     return LPK_INVALID_ARG;
@@ -1339,8 +1395,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       const SmemPlan L = plan_smem(P, use_cs, sizeof(double) << s2, f32 ? 4 : 8, ctx->resident_mode == 0);
       smem = L.total;
       if (smem > SMEM_LIMIT) continue;
-      LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(cfn, cudaFuncAttributeNonPortableClusterSizeAllowed, use_cs > 8 ? 1 : 0));
+      LPK_CUDA_TRY(ctx, prepare_fn(cfn));
       cfg.gridDim = dim3(use_cs);
       cfg.blockDim = dim3(KTPB);
       cfg.dynamicSmemBytes = smem;
@@ -1363,7 +1418,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
     if (use_cs < 2) use_cs = 0;
     int emode, ecs;
     exec_mode(ctx, P, &emode, &ecs);
-    if (use_cs == 0 && emode == 2) {
+    if (use_cs == 0 && (emode == 2 || emode == 3)) {
       ctx->err = "no cluster configuration of the persistent kernel can be scheduled";
       return LPK_CUDA_ERROR;
     }
@@ -1378,7 +1433,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       ctx->err = "too many colors for the shared-memory sweep state";
       return LPK_INVALID_ARG;
     }
-    LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+    LPK_CUDA_TRY(ctx, prepare_fn(gfn));
     int per_sm = 0;
     LPK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfn, KTPB, gsmem));
     if (per_sm < 1) {
@@ -1623,7 +1678,7 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
     ctx->err = "too many colors for the shared-memory sweep state";
     return LPK_INVALID_ARG;
   }
-  LPK_CUDA_TRY(ctx, cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem));
+  LPK_CUDA_TRY(ctx, prepare_fn(gfn));
   apply_plan(A, L);
   A.u_shift = 0;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(KrylovCtl), ctx->stream));

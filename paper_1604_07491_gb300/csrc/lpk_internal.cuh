@@ -55,6 +55,12 @@ struct DevProblem {
   int tuned = 0, tuned_mode = 0, tuned_cs = 0;
   double tuned_us[4] = {0, 0, 0, 0};  // time per Krylov iteration of grid, cluster 16, 8, 4
 
+  cudaStream_t stream = nullptr;  // the owning context's stream (frees are ordered on it)
+
+  // interior-point workspace (allocated on the first lp_solve)
+  size_t ipm_bytes = 0;
+  double *ipm_buf = nullptr;
+
   // Krylov workspace (allocated on first use)
   size_t ws_bytes = 0;
   void *ws = nullptr;
@@ -87,7 +93,7 @@ struct lpk_ctx {
   int red_blocks = 0;
 
   // execution path of the persistent Krylov kernel (lpk_set_exec)
-  int cluster_mode = 0;          // 0 auto, 1 grid, 2 cluster
+  int cluster_mode = 0;          // 0 auto, 1 grid, 2 cluster, 3 batch
   int cluster_size_override = 0; // 0: chosen from nnz
   int last_cluster = 0;          // cluster size of the last launch (0: grid)
   int resident_mode = 0;         // 0: rows cached in shared memory when they fit, 1: never
@@ -102,6 +108,15 @@ struct lpk_ctx {
   double *kpart = nullptr;       // per-CTA partials of the persistent kernels
   int kgrid_cache[8] = {0};      // cooperative grid sizes per kernel variant
 };
+
+// Device memory (devmem.cu): stream-ordered allocation on the context's
+// stream from the library's pool; dev_free is ordered on the given stream.
+cudaError_t dev_alloc_bytes(lpk_ctx *ctx, void **p, size_t bytes);
+void dev_free(cudaStream_t s, void *p);
+template <typename T>
+inline cudaError_t dev_alloc(lpk_ctx *ctx, T **p, size_t count) {
+  return dev_alloc_bytes(ctx, (void **)p, sizeof(T) * (count > 0 ? count : 1));
+}
 
 constexpr int RED_MAX_SLOTS = 24;
 constexpr int RED_THREADS = 256;

@@ -278,21 +278,18 @@ __global__ void k_inrow_of_pos(int mr, const int *perm, const int *in_row_of_red
 
 inline int nblk(long long n, int t = TPB) { return (int)((n + t - 1) / t); }
 
-template <typename T>
-cudaError_t dmalloc(T **p, size_t count) {
-  return cudaMalloc((void **)p, sizeof(T) * (count > 0 ? count : 1));
-}
-
-struct Scratch {  // device temporaries freed at the end of prepare
+struct Scratch {  // device temporaries of prepare, freed (stream-ordered) at its end
+  lpk_ctx *ctx;
   std::vector<void *> ptrs;
+  explicit Scratch(lpk_ctx *c) : ctx(c) {}
   template <typename T>
   cudaError_t get(T **p, size_t count) {
-    cudaError_t e = dmalloc(p, count);
+    cudaError_t e = dev_alloc(ctx, p, count);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
   }
   ~Scratch() {
-    for (void *p : ptrs) cudaFree(p);
+    for (void *p : ptrs) dev_free(ctx->stream, p);
   }
 };
 
@@ -302,9 +299,8 @@ void free_problem(DevProblem &P) {
   void *ptrs[] = {P.pos_of_in_row, P.in_row_of_pos, P.col_of_in, P.in_col_of, P.color_in, P.rp,
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
-                  P.gm_V};
-  for (void *p : ptrs)
-    if (p) cudaFree(p);
+                  P.gm_V,          P.ipm_buf};
+  for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }
 
@@ -312,9 +308,10 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   cudaStream_t st = ctx->stream;
   const int m = A->m, n = A->n;
   const long long nnz = A->nnz;
+  P.stream = st;
   P.m_in = m;
   P.n_in = n;
-  Scratch S;
+  Scratch S(ctx);
   long long *rp_in;
   int *ci_in;
   double *val_in;
@@ -380,8 +377,8 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   P.nnz = nnz;
   P.has_empty_rows = mr < m;
   P.has_empty_cols = nr < n;
-  LPK_CUDA_TRY(ctx, dmalloc(&P.col_of_in, n));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.in_col_of, nr));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.col_of_in, n));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.in_col_of, nr));
   if (m > 0) LPK_LAUNCH(ctx, k_keepmap, nblk(m), TPB, 0, st, m, rowcnt, rscan, row_map, red_row);
   if (n > 0) LPK_LAUNCH(ctx, k_keepmap, nblk(n), TPB, 0, st, n, colcnt, cscan, P.col_of_in, P.in_col_of);
   (void)col_map_tmp;
@@ -469,34 +466,34 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
     for (int c = 0; c < nc; ++c) P.color_ptr_h[c] = hs[(size_t)c * nb];
     P.color_ptr_h[nc] = mr;
   }
-  LPK_CUDA_TRY(ctx, dmalloc(&P.color_ptr, nc + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.color_ptr, nc + 1));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.color_ptr, P.color_ptr_h.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, st));
   // ---- permuted CSR ---------------------------------------------------------
-  LPK_CUDA_TRY(ctx, dmalloc(&P.rp, mr + 1));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.ci, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.a, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.src, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.ah64, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.ah32, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.rho, mr));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rp, mr + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ci, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.a, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.src, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah64, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah32, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rho, mr));
   if (mr > 0) LPK_LAUNCH(ctx, k_perm_rowlen, nblk(mr), TPB, 0, st, mr, perm, rp_red, rlen);
   LPK_LAUNCH(ctx, k_scan<int>, 1, 1024, 0, st, mr, rlen, P.rp);
   if (mr > 0)
     LPK_LAUNCH(ctx, k_perm_fill, nblk(mr), TPB, 0, st, mr, perm, red_row, rp_in, val_in, ci_red, rp_red, P.rp, P.ci, P.a,
                                            P.src);
   // ---- CSC of the permuted matrix -------------------------------------------
-  LPK_CUDA_TRY(ctx, dmalloc(&P.cp, nr + 1));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.ri, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.at, nnz));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.aht, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.cp, nr + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ri, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.at, nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.aht, nnz));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.cp, cp_red, sizeof(int) * (nr + 1), cudaMemcpyDeviceToDevice, st));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(cursor, cp_red, sizeof(int) * (nr > 0 ? nr : 1), cudaMemcpyDeviceToDevice, st));
   if (mr > 0) LPK_LAUNCH(ctx, k_csc_fill, nblk(mr), TPB, 0, st, mr, P.rp, P.ci, P.a, cursor, P.ri, P.at);
   if (nr > 0) LPK_LAUNCH(ctx, k_csc_sort, nblk(nr), TPB, 0, st, nr, P.cp, P.ri, P.at);
   // ---- maps to the input numbering ------------------------------------------
-  LPK_CUDA_TRY(ctx, dmalloc(&P.pos_of_in_row, m));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.color_in, m));
-  LPK_CUDA_TRY(ctx, dmalloc(&P.in_row_of_pos, mr));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.pos_of_in_row, m));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.color_in, m));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.in_row_of_pos, mr));
   if (m > 0) LPK_LAUNCH(ctx, k_compose, nblk(m), TPB, 0, st, m, row_map, pos_of_red, color, P.pos_of_in_row, P.color_in);
   if (mr > 0) LPK_LAUNCH(ctx, k_inrow_of_pos, nblk(mr), TPB, 0, st, mr, perm, red_row, P.in_row_of_pos);
   P.rp_h.assign(mr + 1, 0);

@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREA
           6: "EMPTY_ROW_INCONSISTENT", 7: "EMPTY_COL_UNBOUNDED", 8: "INVALID_ARG", 9: "OOM",
           10: "CUDA_ERROR"}
 MRNE, CGNE, ABGMRES = 0, 1, 2
-EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER, EXEC_NO_RESIDENT = 0, 1, 2, 4
+EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER, EXEC_BATCH, EXEC_NO_RESIDENT = 0, 1, 2, 3, 4
 FP64, MIXED = 0, 1
 NE_SSOR, NE_SOR = 0, 1
 
@@ -29,7 +29,9 @@ NE_SSOR, NE_SOR = 0, 1
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
            "lpk_reset_stats", "lpk_set_exec", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
-           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_lp_solve"]
+           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_lp_solve",
+           "lpk_lp_solve_batch", "lpk_server_default_config", "lpk_server_create", "lpk_server_destroy",
+           "lpk_server_now", "lpk_server_submit", "lpk_server_wait", "lpk_server_stats"]
 
 
 class LpkError(RuntimeError):
@@ -83,6 +85,33 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("lanes", C.c_int32), ("mem_budget", C.c_int64),
+                ("color_seed", C.c_uint64)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("info", Info), ("status", C.c_int32), ("lane", C.c_int32), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_end", C.c_double), ("mem_bytes", C.c_int64),
+                ("error", C.c_char * 256)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("info", "error")}
+        d["info"] = self.info.as_dict()
+        d["status_name"] = STATUS.get(self.status, str(self.status))
+        d["error"] = self.error.decode(errors="replace")
+        return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("pending", C.c_int64), ("running", C.c_int64), ("completed", C.c_int64),
+                ("mem_in_use", C.c_int64), ("mem_peak", C.c_int64), ("mem_budget", C.c_int64),
+                ("lanes", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _lib = None
 
 
@@ -114,6 +143,15 @@ def load():
         "lpk_lp_solve": (I32, [P, P, P, P, C.POINTER(Options), P, P, P, C.POINTER(Info), I32]),
         "lpk_ne_solve_noalloc": (I32, [P, P, P, P, I32, D, I32, I32, D, I32, P, P,
                                        C.POINTER(KrylovInfo)]),
+        "lpk_lp_solve_batch": (I32, [I32, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(Options),
+                                     C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(Info), I32]),
+        "lpk_server_default_config": (None, [C.POINTER(ServerConfig)]),
+        "lpk_server_create": (I32, [C.POINTER(P), C.POINTER(ServerConfig)]),
+        "lpk_server_destroy": (None, [P]),
+        "lpk_server_now": (D, [P]),
+        "lpk_server_submit": (I32, [P, C.POINTER(Matrix), P, P, C.POINTER(Options), C.POINTER(I64)]),
+        "lpk_server_wait": (I32, [P, I64, D, P, P, P, C.POINTER(RequestResult)]),
+        "lpk_server_stats": (I32, [P, C.POINTER(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -206,7 +244,8 @@ class Context:
         load().lpk_reset_stats(self._h)
 
     def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
-        """Krylov kernel path: EXEC_AUTO, EXEC_GRID or EXEC_CLUSTER (size 0/2/4/8/16)."""
+        """Krylov kernel path: EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER or EXEC_BATCH
+        (cluster size 0/2/4/8/16; or-ing EXEC_NO_RESIDENT disables the row cache)."""
         _check(self._h, load().lpk_set_exec(self._h, exec_mode, cluster_size))
 
 
@@ -346,3 +385,100 @@ class Problem:
         if st not in (OK, MAX_IPM_ITER, DIVERGED):
             _check(self.ctx.handle, st)
         return x, y, s, info.as_dict()
+
+
+def solve_batch(problems, bs, cs, outs=None, options: Options | None = None, **kw):
+    """lpk_lp_solve_batch: LP i = (problems[i], bs[i], cs[i]), each problem on
+    its own Context, solved side by side.  Returns a list of (x, y, s, info)."""
+    k = len(problems)
+    o = options if options is not None else default_options(**kw)
+    bs = [_f64(b) for b in bs]
+    cs = [_f64(c) for c in cs]
+    if outs is None:
+        outs = [(_like(cs[i], p.n), _like(bs[i], p.m), _like(cs[i], p.n)) for i, p in enumerate(problems)]
+    devs = {_ptr(v)[1] for v in bs + cs + [a for t in outs for a in t]}
+    if len(devs) > 1:
+        raise ValueError("all vectors must be on the device or all on the host")
+    arr = C.c_void_p * max(k, 1)
+    infos = (Info * max(k, 1))()
+    st = load().lpk_lp_solve_batch(
+        k, arr(*[p._h for p in problems]), arr(*[_ptr(b)[0] for b in bs]), arr(*[_ptr(c)[0] for c in cs]),
+        C.byref(o), arr(*[_ptr(t[0])[0] for t in outs]), arr(*[_ptr(t[1])[0] for t in outs]),
+        arr(*[_ptr(t[2])[0] for t in outs]), infos, devs.pop() if devs else 0)
+    res = [(outs[i][0], outs[i][1], outs[i][2], infos[i].as_dict()) for i in range(k)]
+    if st not in (OK, MAX_IPM_ITER, DIVERGED, KRYLOV_STALL) and k > 0:
+        bad = [i for i in range(k) if infos[i].status == st]
+        if bad:   # a solve failed
+            _check(problems[bad[0]].ctx.handle, st)
+        # rejected before anything ran: the offending context holds the message
+        msgs = sorted({p.ctx.last_error() for p in problems} - {""})
+        raise LpkError(st, "; ".join(msgs))
+    return res
+
+
+class Server:
+    """lpk_server_*: continuous batching of LPs on one GPU (host CSR in,
+    host vectors out)."""
+
+    def __init__(self, device=0, lanes=16, mem_budget=0, color_seed=0x5EED):
+        lib = load()
+        cfg = ServerConfig()
+        lib.lpk_server_default_config(C.byref(cfg))
+        cfg.device, cfg.lanes, cfg.mem_budget, cfg.color_seed = device, lanes, int(mem_budget), color_seed
+        self._h = C.c_void_p()
+        st = lib.lpk_server_create(C.byref(self._h), C.byref(cfg))
+        if st != OK:
+            raise LpkError(st, "lpk_server_create failed")
+        self._dims = {}
+
+    def submit(self, m, n, row_ptr, col_idx, val, b, c, options: Options | None = None, **kw) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        b, c = np.ascontiguousarray(b, np.float64), np.ascontiguousarray(c, np.float64)
+        A = Matrix(m=int(m), n=int(n), nnz=int(rp[-1]), row_ptr=rp.ctypes.data, col_idx=ci.ctypes.data,
+                   val=v.ctypes.data, on_device=0)
+        o = options if options is not None else default_options(**kw)
+        t = C.c_int64()
+        st = load().lpk_server_submit(self._h, C.byref(A), C.c_void_p(b.ctypes.data),
+                                      C.c_void_p(c.ctypes.data), C.byref(o), C.byref(t))
+        if st != OK:
+            raise LpkError(st, "lpk_server_submit failed")
+        self._dims[t.value] = (int(m), int(n))
+        return t.value
+
+    def submit_lp(self, lp, **kw) -> int:
+        return self.submit(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, lp.b, lp.c, **kw)
+
+    def wait(self, ticket, timeout=-1.0):
+        """(x, y, s, result dict), or None if not ready within timeout seconds."""
+        m, n = self._dims[ticket]
+        x, y, s = np.empty(n), np.empty(m), np.empty(n)
+        r = RequestResult()
+        st = load().lpk_server_wait(self._h, ticket, float(timeout), C.c_void_p(x.ctypes.data),
+                                    C.c_void_p(y.ctypes.data), C.c_void_p(s.ctypes.data), C.byref(r))
+        if st == TIMEOUT:
+            return None
+        if st != OK:
+            raise LpkError(st, "lpk_server_wait failed")
+        del self._dims[ticket]
+        return x, y, s, r.as_dict()
+
+    def now(self) -> float:
+        return load().lpk_server_now(self._h)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        load().lpk_server_stats(self._h, C.byref(st))
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            load().lpk_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

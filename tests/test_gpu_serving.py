@@ -1,0 +1,175 @@
+"""Many LPs on one GPU: the batched solve (lpk_lp_solve_batch) and the
+continuous-batching server (lpk_server_*), through the C ABI.
+
+The property that matters: an LP gives the same result alone and in a mix.
+Lanes run the batch path (cluster size fixed by the problem, reductions in a
+fixed order), so "the same" is bitwise here -- stricter than the objective
+tolerance of 1e-7 that the oracle comparison uses.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1604_07491_gb300 import gen  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def lpk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07491_gb300 import build, lpk as L
+    build.build()
+    return L
+
+
+def certs(lp, x, y, s):
+    A = lp.scipy()
+    pinf = np.linalg.norm(lp.b - A @ x) / max(np.linalg.norm(lp.b), 1)
+    dinf = np.linalg.norm(lp.c - A.T @ y - s) / max(np.linalg.norm(lp.c), 1)
+    gap = abs(lp.c @ x - lp.b @ y) / (1 + abs(lp.c @ x))
+    return pinf, dinf, gap
+
+
+def mix():
+    """LPs of different sizes and shapes (tiny, serving-stream sizes, medium family)."""
+    return [
+        (gen.tiny_lp(), dict(inner_sweeps=1)),
+        (gen.serving_lp(4), dict(solver=2, inner_sweeps=3)),            # m = 121
+        (gen.serving_lp(1), dict(solver=2, inner_sweeps=3)),            # m = 219
+        (gen.medium_lp(0.0123), dict(inner_sweeps=3, max_krylov=3 * 246)),
+        (gen.tiny_lp(seed=gen.SEED_BASE + 77), dict(inner_sweeps=1, precision=1)),
+    ]
+
+
+_ALONE = {}
+
+
+def solve_alone(lpk, k, lp, opts):
+    """LP k of mix() on its own, on the batch path (cached per module)."""
+    if k not in _ALONE:
+        ctx = lpk.Context(0)
+        ctx.set_exec(lpk.EXEC_BATCH)
+        P = lpk.Problem.from_lp(ctx, lp)
+        x, y, s, info = P.lp_solve(lp.b, lp.c, **opts)
+        cs = ctx.stats()["last_cluster_size"]
+        ctx.close()
+        _ALONE[k] = (x, y, s, info, cs)
+    return _ALONE[k]
+
+
+def test_batch_equals_alone_bitwise(lpk, orc):
+    cases = mix()
+    alone = [solve_alone(lpk, k, lp, o) for k, (lp, o) in enumerate(cases)]
+    for (lp, o), (x, y, s, info, cs) in zip(cases, alone):
+        assert info["status_name"] == "OK", (lp.name, info)
+        assert cs in (4, 8, 16)
+        pinf, dinf, gap = certs(lp, x, y, s)
+        assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+    # the same LPs side by side, each on its own context and stream; one batch
+    # call takes one option set, so the cases are grouped by options
+    groups = {}
+    for i, (lp, o) in enumerate(cases):
+        groups.setdefault(tuple(sorted(o.items())), []).append(i)
+    streams = [torch.cuda.Stream() for _ in cases]
+    ctxs = [lpk.Context(0, streams[i].cuda_stream) for i in range(len(cases))]
+    try:
+        for key, idx in groups.items():
+            probs = [lpk.Problem.from_lp(ctxs[i], cases[i][0]) for i in idx]
+            res = lpk.solve_batch(probs, [cases[i][0].b for i in idx], [cases[i][0].c for i in idx],
+                                  **dict(key))
+            for i, (x, y, s, info) in zip(idx, res):
+                ax, ay, as_, ainfo, _ = alone[i]
+                assert info["status_name"] == "OK"
+                assert np.array_equal(x, ax) and np.array_equal(y, ay) and np.array_equal(s, as_), cases[i][0].name
+                assert info["ipm_iters"] == ainfo["ipm_iters"]
+                assert info["krylov_iters_total"] == ainfo["krylov_iters_total"]
+    finally:
+        for c in ctxs:
+            c.close()
+    # and against the oracle (objective within 1e-7)
+    for (lp, o), (x, y, s, info, cs) in zip(cases[:3], alone[:3]):
+        ok = dict(o)
+        if "solver" in ok:
+            ok["method"] = ok.pop("solver")
+        ok.pop("precision", None)
+        ox, oy, os_, oinfo = orc.lp_solve_lp(lp, **ok)
+        assert oinfo["status_name"] == "OK"
+        assert abs(info["obj_primal"] - oinfo["obj_primal"]) <= 1e-7 * max(1.0, abs(oinfo["obj_primal"]))
+
+
+def test_batch_rejects_shared_context_and_grid(lpk):
+    lp = gen.tiny_lp()
+    ctx = lpk.Context(0)
+    P1 = lpk.Problem.from_lp(ctx, lp)
+    P2 = lpk.Problem.from_lp(ctx, lp)
+    with pytest.raises(lpk.LpkError) as e:
+        lpk.solve_batch([P1, P2], [lp.b, lp.b], [lp.c, lp.c])
+    assert e.value.status == lpk.INVALID_ARG and "own context" in str(e.value)
+    ctx2 = lpk.Context(0)
+    ctx2.set_exec(lpk.EXEC_GRID)
+    P3 = lpk.Problem.from_lp(ctx2, lp)
+    with pytest.raises(lpk.LpkError) as e:
+        lpk.solve_batch([P1, P3], [lp.b, lp.b], [lp.c, lp.c])
+    assert "grid path" in str(e.value)
+    ctx.close()
+    ctx2.close()
+
+
+def test_server_alone_vs_in_mix(lpk):
+    """Requests arrive while others run (continuous batching); every result is
+    bitwise the one the same LP gives alone on the batch path."""
+    cases = mix()
+    alone = [solve_alone(lpk, k, lp, o) for k, (lp, o) in enumerate(cases)]
+    srv = lpk.Server(0, lanes=3)
+    try:
+        tickets = []
+        for k, (lp, o) in enumerate(cases):
+            tickets.append(srv.submit_lp(lp, **o))
+            if k == 1:
+                time.sleep(0.05)   # later requests arrive while the first ones run
+        results = [srv.wait(t, timeout=300.0) for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    lanes_used = set()
+    for (lp, o), r, a in zip(cases, results, alone):
+        assert r is not None, lp.name
+        x, y, s, res = r
+        assert res["status_name"] == "OK" and res["info"]["status_name"] == "OK", res
+        assert np.array_equal(x, a[0]) and np.array_equal(y, a[1]) and np.array_equal(s, a[2]), lp.name
+        assert res["t_submit"] <= res["t_start"] <= res["t_end"]
+        lanes_used.add(res["lane"])
+    assert len(lanes_used) >= 2          # the work was spread over lanes
+    assert st["completed"] == len(cases) and st["running"] == 0 and st["pending"] == 0
+    assert st["mem_in_use"] == 0 and st["mem_peak"] > 0
+
+
+def test_server_memory_admission_and_errors(lpk):
+    """A budget smaller than any LP: each runs alone (no two admitted at once);
+    a request that fails (inconsistent empty row) does not stop the server."""
+    import scipy.sparse as sp
+    lps = [gen.tiny_lp(seed=gen.SEED_BASE + i) for i in range(3)]
+    srv = lpk.Server(0, lanes=3, mem_budget=1)
+    try:
+        A2 = np.vstack([np.zeros((1, lps[0].n)), lps[0].scipy().toarray()])
+        S = sp.csr_matrix(A2)
+        b2 = np.concatenate([[1.0], lps[0].b])   # empty row with b != 0
+        bad = srv.submit(S.shape[0], S.shape[1], S.indptr, S.indices, S.data, b2, lps[0].c)
+        good = [srv.submit_lp(lp) for lp in lps]
+        rb = srv.wait(bad, timeout=120.0)
+        rg = [srv.wait(t, timeout=120.0) for t in good]
+    finally:
+        srv.close()
+    assert rb[3]["status_name"] == "EMPTY_ROW_INCONSISTENT" and "empty row" in rb[3]["error"]
+    spans = sorted((r[3]["t_start"], r[3]["t_end"]) for r in rg + [rb])
+    for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+        assert b0 >= a1                    # never two LPs on the device at once
+    for lp, r in zip(lps, rg):
+        assert r[3]["status_name"] == "OK"
+        pinf, dinf, gap = certs(lp, *r[:3])
+        assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
