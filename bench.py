@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--serving-count", type=int, default=48, help="serving: LPs of the stream replayed")
     ap.add_argument("--lanes", type=int, default=16, help="serving: server lanes")
+    ap.add_argument("--serving-max-m", type=int, default=0,
+                    help="serving: replay only the stream's LPs with m <= this (0: all)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     opts = dict(wl["opts"])
@@ -458,8 +460,17 @@ def run_serving(args, wl, opts, lpk, local, rank, world, barrier):
     submitted at its arrival time; latency = result ready - arrival."""
     from paper_1604_07491_gb300 import gen
     N = args.serving_count
-    arrivals = gen.serving_arrivals(N)
-    lps = [make_lp("serving", seed_offset=rank * N + i) for i in range(N)]
+    # the stream's LPs in arrival order, optionally only those with m <= max_m
+    # (each keeps its own arrival time; the stream is thinned, not re-timed)
+    arrivals_all = gen.serving_arrivals(200000)
+    lps, arrivals = [], []
+    i = rank * 100000
+    while len(lps) < N:
+        lp = make_lp("serving", seed_offset=i)
+        if args.serving_max_m <= 0 or lp.m <= args.serving_max_m:
+            lps.append(lp)
+            arrivals.append(arrivals_all[i - rank * 100000])
+        i += 1
     prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
     srv = lpk.Server(local, lanes=args.lanes)
     # warm-up: a few small LPs (kernel loading, pool growth)
@@ -489,6 +500,8 @@ def run_serving(args, wl, opts, lpk, local, rank, world, barrier):
         "vs_baseline": None, "dtype": "f32 values / f64 accumulation" if prec == lpk.MIXED else "f64",
         "data": "synthetic",
         "config": {"workload": f"serving: {wl['desc']}", "lps": N, "lanes": args.lanes,
+                   "stream": ("the first LPs of the stream" if args.serving_max_m <= 0 else
+                              f"the first LPs of the stream with m <= {args.serving_max_m} (thinned stream)"),
                    "m_range": [min(lp.m for lp in lps), max(lp.m for lp in lps)], "precision": args.precision,
                    "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]], "inner_sweeps": opts["inner_sweeps"],
                    "l2": "inputs of every LP differ (no reuse)", "inputs": "host CSR submitted at arrival"},

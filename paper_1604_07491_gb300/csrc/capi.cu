@@ -42,7 +42,7 @@ struct Vec {
   ~Vec() {
     if (owned && dev) {
       dev_free(ctx->stream, dev);
-      cudaStreamSynchronize(ctx->stream);  // outputs are in the caller's host buffer on return
+      ctx_sync(ctx);  // outputs are in the caller's host buffer on return
     }
   }
 };
@@ -89,7 +89,7 @@ lpk_status check_d2(lpk_ctx *ctx, const DevProblem &P, const double *d2_int) {
   int h = 0;
   cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
   dev_free(ctx->stream, bad);
-  cudaStreamSynchronize(ctx->stream);
+  ctx_sync(ctx);
   if (h) {
     ctx->err = "d2 must be positive and finite";
     return LPK_INVALID_ARG;
@@ -132,6 +132,7 @@ LPK_API void lpk_destroy(lpk_ctx *ctx) {
   dev_free(ctx->stream, ctx->kctl);
   dev_free(ctx->stream, ctx->kpart);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->ev_block) cudaEventDestroy(ctx->ev_block);
   if (ctx->h_red) cudaFreeHost(ctx->h_red);
   if (ctx->h_kctl) cudaFreeHost(ctx->h_kctl);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -220,7 +221,7 @@ LPK_API void lpk_problem_free(lpk_problem *P) {
   if (P->ctx) {  // null once its context was destroyed (device memory already released)
     lpk_ctx *ctx = P->ctx;
     cudaSetDevice(ctx->device);
-    cudaStreamSynchronize(ctx->stream);
+    ctx_sync(ctx);
     free_problem(P->d);
     for (size_t i = 0; i < ctx->problems.size(); ++i)
       if (ctx->problems[i] == P) {
@@ -250,7 +251,7 @@ LPK_API lpk_status lpk_problem_coloring(lpk_ctx *ctx, const lpk_problem *P, int3
     LPK_CUDA_TRY(ctx, cudaMemcpyAsync(color, d.color_in, sizeof(int) * d.m_in, cudaMemcpyDeviceToHost, ctx->stream));
   if (perm && d.m)
     LPK_CUDA_TRY(ctx, cudaMemcpyAsync(perm, d.in_row_of_pos, sizeof(int) * d.m, cudaMemcpyDeviceToHost, ctx->stream));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   if (color_ptr) std::memcpy(color_ptr, d.color_ptr_h.data(), sizeof(int) * d.color_ptr_h.size());
   return LPK_OK;
 }
@@ -277,7 +278,7 @@ LPK_API lpk_status lpk_scale_rows(lpk_ctx *ctx, lpk_problem *P, const double *d2
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   TRY(vrho.finish());
   TRY(vah.finish());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return LPK_OK;
 }
 
@@ -306,7 +307,7 @@ LPK_API lpk_status lpk_spmv(lpk_ctx *ctx, lpk_problem *P, int32_t transpose, con
   }
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   TRY(vy.finish());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return LPK_OK;
 }
 
@@ -340,7 +341,7 @@ LPK_API lpk_status lpk_sweep(lpk_ctx *ctx, lpk_problem *P, const double *d2, con
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   TRY(vz.finish());
   TRY(vu.finish());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return LPK_OK;
 }
 
@@ -378,7 +379,7 @@ LPK_API lpk_status lpk_ne_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, 
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   TRY(vdy.finish());
   TRY(vdw.finish());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   if (kinfo) {
     kinfo->iters = kr.iters;
     kinfo->converged = kr.converged;
@@ -420,7 +421,7 @@ LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, c
   lpk_info inf;
   lpk_status st = lp_solve_dev(ctx, d, vb.dev, vc.dev, o, vx.dev, vy.dev, vs.dev, inf);
   cudaEventRecord(e1, ctx->stream);
-  cudaEventSynchronize(e1);
+  ctx_sync(ctx);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
@@ -431,7 +432,7 @@ LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, c
     TRY(vx.finish());
     TRY(vy.finish());
     TRY(vs.finish());
-    LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   }
   return st;
 }

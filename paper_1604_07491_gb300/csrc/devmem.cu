@@ -54,3 +54,19 @@ cudaError_t dev_alloc_bytes(lpk_ctx *ctx, void **p, size_t bytes) {
 void dev_free(cudaStream_t s, void *p) {
   if (p) cudaFreeAsync(p, s);
 }
+
+// Host waits on the context's stream.  Alone, a context spins in the driver
+// (lowest wake-up latency).  On the batch path many contexts wait at once,
+// one host thread each; spinning threads would then take every host core and
+// delay each other's next launch by whole scheduler periods, so those waits
+// block on an event created for blocking synchronisation instead.
+cudaError_t ctx_sync(lpk_ctx *ctx) {
+  if (ctx->cluster_mode != 3) return cudaStreamSynchronize(ctx->stream);
+  if (!ctx->ev_block) {
+    cudaError_t e = cudaEventCreateWithFlags(&ctx->ev_block, cudaEventBlockingSync | cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(ctx->ev_block, ctx->stream);
+  if (e != cudaSuccess) return e;
+  return cudaEventSynchronize(ctx->ev_block);
+}

@@ -274,7 +274,7 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
       LPK_LAUNCH(ctx, k_check_empty, eb(len), TPB, 0, st, P.m_in, P.n_in, P.pos_of_in_row, P.col_of_in, b_in, c_in, flags);
     int hf = 0;
     cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
+    ctx_sync(ctx);
     if (hf & 4) {
       ctx->err = "b or c has a non-finite entry";
       info.status = LPK_INVALID_ARG;
@@ -429,6 +429,6 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
   scatter_n(ctx, P, s, s_in, nullptr);
   if (P.n_in > P.n) LPK_LAUNCH(ctx, k_scatter_fill_s, eb(P.n_in), TPB, 0, st, P.n_in, P.col_of_in, c_in, s_in);
   LPK_CUDA_TRY(ctx, cudaGetLastError());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return (lpk_status)status;
 }

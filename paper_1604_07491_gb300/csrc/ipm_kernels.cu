@@ -145,7 +145,7 @@ lpk_status red_fetch(lpk_ctx *ctx, int nslots) {
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_red, ctx->red_out, sizeof(double) * nslots, cudaMemcpyDeviceToHost,
                                     ctx->stream));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return LPK_OK;
 }
 

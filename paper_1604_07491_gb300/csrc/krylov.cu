@@ -1456,7 +1456,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   }
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_kctl, ctx->kctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, ctx->stream));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   const KrylovCtl *h = (const KrylovCtl *)ctx->h_kctl;
   float ms = 0.f;
   LPK_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));

@@ -83,6 +83,7 @@ struct lpk_ctx {
   int verbose = 0;               // from lpk_options.verbose of the running solve
   lpk_stats stats{};             // see lpk_get_stats
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_block = nullptr;  // blocking-sync event of ctx_sync
 
   // reductions of the elementwise kernels: per-block partials + completion
   // counter, the last block reduces in fixed order (deterministic)
@@ -112,6 +113,8 @@ struct lpk_ctx {
 // Device memory (devmem.cu): stream-ordered allocation on the context's
 // stream from the library's pool; dev_free is ordered on the given stream.
 cudaError_t dev_alloc_bytes(lpk_ctx *ctx, void **p, size_t bytes);
+// Wait for the context's stream (blocking, not spinning, on the batch path).
+cudaError_t ctx_sync(lpk_ctx *ctx);
 void dev_free(cudaStream_t s, void *p);
 template <typename T>
 inline cudaError_t dev_alloc(lpk_ctx *ctx, T **p, size_t count) {

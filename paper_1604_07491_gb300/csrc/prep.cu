@@ -323,7 +323,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
     long long ends[2];
     LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&ends[0], rp_in, sizeof(long long), cudaMemcpyDeviceToHost, st));
     LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&ends[1], rp_in + m, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    LPK_CUDA_TRY(ctx, ctx_sync(ctx));
     if (ends[0] != 0 || ends[1] != nnz) {
       ctx->err = "row_ptr[0] must be 0 and row_ptr[m] must equal nnz";
       return LPK_INVALID_ARG;
@@ -346,7 +346,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   if (m > 0) LPK_LAUNCH(ctx, k_validate, nblk(m), TPB, 0, st, m, n, rp_in, ci_in, val_in, err);
   int herr = 0;
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   if (herr) {
     const char *msg[] = {"", "row_ptr decreases", "column index out of range", "non-finite value",
                          "column indices not strictly increasing within a row"};
@@ -371,7 +371,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   int mr = 0, nr = 0;
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&mr, rscan + m, sizeof(int), cudaMemcpyDeviceToHost, st));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&nr, cscan + n, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   P.m = mr;
   P.n = nr;
   P.nnz = nnz;
@@ -426,7 +426,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
                                               round + b, remaining + b);
     int rem[burst];
     LPK_CUDA_TRY(ctx, cudaMemcpyAsync(rem, remaining, sizeof(int) * burst, cudaMemcpyDeviceToHost, st));
-    LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    LPK_CUDA_TRY(ctx, ctx_sync(ctx));
     round += burst;
     if (rem[burst - 1] == 0) break;
     if (round > mr + 8) {
@@ -440,7 +440,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   if (mr > 0) LPK_LAUNCH(ctx, k_max, nblk(mr), TPB, 0, st, mr, color, cmax);
   int hmax = -1;
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(&hmax, cmax, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   const int nc = hmax + 1;
   P.n_colors = nc;
   // ---- rows sorted by (color, row) ------------------------------------------
@@ -462,7 +462,7 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
     std::vector<int> hs((size_t)nc * nb + 1);
     if (mr > 0)
       LPK_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), hscan, sizeof(int) * hs.size(), cudaMemcpyDeviceToHost, st));
-    LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    LPK_CUDA_TRY(ctx, ctx_sync(ctx));
     for (int c = 0; c < nc; ++c) P.color_ptr_h[c] = hs[(size_t)c * nb];
     P.color_ptr_h[nc] = mr;
   }
@@ -499,6 +499,6 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   P.rp_h.assign(mr + 1, 0);
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.rp_h.data(), P.rp, sizeof(int) * (mr + 1), cudaMemcpyDeviceToHost, st));
   LPK_CUDA_TRY(ctx, cudaGetLastError());
-  LPK_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
   return LPK_OK;
 }
