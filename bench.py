@@ -29,6 +29,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# one hardware work queue per stream: with the default of 8, the streams of
+# more than 8 lanes share queues and a persistent kernel of one lane would
+# hold back the launches of another (read when the CUDA context is created)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "LPs solved/s & p99 latency at gap≤1e-8 (mixed vs FP64); NE-sweep HBM GB/s"
 UNIT = "LPs/s"

@@ -609,21 +609,45 @@ __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, d
 }
 
 // out = A_hat^T x in double through the CSC (thread per column: the columns
-// are short, and independent columns keep many loads in flight); returns
-// this thread's share of ||out||^2 and, if dot_old != nullptr, adds its share
-// of (old, out) where old is read before out is written (old may alias out)
+// are short).  Each thread works on CW columns at once (j, j + NT, ...), so
+// the dependent loads column pointer -> row index -> x of different columns
+// are in flight together instead of one column after the other.  Returns this
+// thread's share of ||out||^2 and, if dot_old != nullptr, adds its share of
+// (old, out) where old is read before out is written (old may alias out).
 template <typename GRP>
 __device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, const double *x, double *out,
                                                double *dot_old = nullptr) {
+  constexpr int CW = 4;
   const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
   double acc = 0.0;
-  for (int j = tid; j < A.n; j += NT) {
-    const int q0 = __ldg(A.cp + j), q1 = __ldg(A.cp + j + 1);
-    double s = 0.0;
-    for (int q = q0; q < q1; ++q) s += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
-    if (dot_old) *dot_old += ldcg(out + j) * s;
-    out[j] = s;
-    acc += s * s;
+  for (int j0 = tid; j0 < A.n; j0 += CW * NT) {
+    int q0[CW], q1[CW];
+    double sv[CW];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int j = j0 + u * NT;
+      q0[u] = j < A.n ? __ldg(A.cp + j) : 0;
+      q1[u] = j < A.n ? __ldg(A.cp + j + 1) : 0;
+      len = max(len, q1[u] - q0[u]);
+      sv[u] = 0.0;
+    }
+    for (int t = 0; t < len; ++t) {
+#pragma unroll
+      for (int u = 0; u < CW; ++u) {
+        const int q = q0[u] + t;
+        if (q < q1[u]) sv[u] += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int j = j0 + u * NT;
+      if (j < A.n) {
+        if (dot_old) *dot_old += ldcg(out + j) * sv[u];
+        out[j] = sv[u];
+        acc += sv[u] * sv[u];
+      }
+    }
   }
   return acc;
 }
@@ -819,6 +843,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       if (cta0) A.gh[0] = gnorm;
       int kk = 0;                  // basis vectors of this cycle
       __shared__ double s_rot[2];
+      __shared__ double s_dot[KWPB][32];
       while (true) {
         if (gnorm <= target) { reason = EXIT_CONV; break; }
         if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
@@ -851,30 +876,54 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         double wn2 = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
           double *h = pass == 0 ? A.h1 : A.h2;
-          // partial dots (w, v_i) over this CTA's rows, thread per basis vector
-          for (int i = threadIdx.x; i <= kk; i += blockDim.x) {
+          // partial dots (w, v_i) over this CTA's rows: lanes over 32 basis
+          // vectors (one coalesced 256-byte load of a row of V), warps over
+          // rows; the warps' partials are summed in warp order in shared memory
+          for (int i0 = 0; i0 <= kk; i0 += 32) {
+            const int i = i0 + lane;
             double acc = 0.0;
-            for (int r = rlo; r < rhi; ++r) acc += ldcg(A.wt + r) * ldcg(A.V + (size_t)r * ld + i);
-            A.gpart[(size_t)b * ld + i] = acc;
+            if (i <= kk) {
+#pragma unroll 4
+              for (int r = rlo + wi; r < rhi; r += KWPB) acc += ldcg(A.wt + r) * ldcg(A.V + (size_t)r * ld + i);
+            }
+            s_dot[wi][lane] = acc;
+            __syncthreads();
+            if (wi == 0 && i <= kk) {
+              double t = 0.0;
+#pragma unroll
+              for (int w = 0; w < KWPB; ++w) t += s_dot[w][lane];
+              A.gpart[(size_t)b * ld + i] = t;
+            }
+            __syncthreads();
           }
           if (!Gp.sync(&s_ok)) return;
           // h_i = sum of the G partials in CTA order, spread over all threads
           for (int i = tid; i <= kk; i += NT) {
             double acc = 0.0;
+#pragma unroll 8
             for (int t = 0; t < G; ++t) acc += ldcg(A.gpart + (size_t)t * ld + i);
             h[i] = acc;
           }
           if (!Gp.sync(&s_ok)) return;
-          // w -= V h on this CTA's rows (a warp per row)
+          // w -= V h on this CTA's rows: a warp per four rows at a time, lanes
+          // over basis vectors (each h_i is loaded once for the four rows)
           double part = 0.0;
-          for (int r = rlo + wi; r < rhi; r += KWPB) {
-            double sacc = 0.0;
-            for (int i = lane; i <= kk; i += 32) sacc += ldcg(h + i) * ldcg(A.V + (size_t)r * ld + i);
-            sacc = warp_sum(sacc);
-            if (lane == 0) {
-              const double w = ldcg(A.wt + r) - sacc;
-              A.wt[r] = w;
-              part += w * w;
+          for (int r0 = rlo + 4 * wi; r0 < rhi; r0 += 4 * KWPB) {
+            double sacc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int i = lane; i <= kk; i += 32) {
+              const double hv = ldcg(h + i);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (r0 + u < rhi) sacc[u] += hv * ldcg(A.V + (size_t)(r0 + u) * ld + i);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const double su = warp_sum(sacc[u]);
+              if (lane == 0 && r0 + u < rhi) {
+                const double w = ldcg(A.wt + r0 + u) - su;
+                A.wt[r0 + u] = w;
+                part += w * w;
+              }
             }
           }
           if (pass == 0) {
@@ -891,30 +940,54 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         Cn.basis += 4 * (kk + 1);  // two passes, each a dot product and an update
         const double hk1 = sqrt(wn2);
         // Givens rotations on column kk of H_bar, computed identically in every
-        // CTA; CTA 0 stores R (packed by columns), cs, sn and the rotated rhs
-        if (threadIdx.x == 0) {
+        // CTA by warp 0; CTA 0 stores R (packed by columns), cs, sn and the
+        // rotated right-hand side.  Applying the earlier rotations is the
+        // affine recurrence hp_{i+1} = -s_i hp_i + c_i h_{i+1}, evaluated 32
+        // entries at a time by a warp scan over the composed affine maps.
+        if (wi == 0) {
           double *Rc = A.R + (size_t)kk * (kk + 1) / 2;
-          double hprev = ldcg(A.h1) + ldcg(A.h2);
-          for (int i = 0; i < kk; ++i) {
-            const double hn = ldcg(A.h1 + i + 1) + ldcg(A.h2 + i + 1);
-            const double c = ldcg(A.cs + i), sg = ldcg(A.sn + i);
-            const double r0 = c * hprev + sg * hn;
-            hprev = -sg * hprev + c * hn;
-            if (b == 0) Rc[i] = r0;
+          double carry = ldcg(A.h1) + ldcg(A.h2);  // hp_0
+          for (int i0 = 0; i0 < kk; i0 += 32) {
+            const int i = i0 + lane;
+            double c = 1.0, sg = 0.0, hn = 0.0;
+            if (i < kk) {
+              hn = ldcg(A.h1 + i + 1) + ldcg(A.h2 + i + 1);
+              c = ldcg(A.cs + i);
+              sg = ldcg(A.sn + i);
+            }
+            // map of entry i: x -> -s x + c h_{i+1} (identity past the end)
+            double Am = i < kk ? -sg : 1.0, Bm = i < kk ? c * hn : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const double Ap = __shfl_up_sync(0xffffffffu, Am, o);
+              const double Bp = __shfl_up_sync(0xffffffffu, Bm, o);
+              if (lane >= o) {
+                Bm = Am * Bp + Bm;
+                Am = Am * Ap;
+              }
+            }
+            const double hp_next = Am * carry + Bm;  // hp_{i+1}
+            double hp_i = __shfl_up_sync(0xffffffffu, hp_next, 1);
+            if (lane == 0) hp_i = carry;
+            if (b == 0 && i < kk) Rc[i] = c * hp_i + sg * hn;
+            carry = __shfl_sync(0xffffffffu, hp_next, 31);
           }
-          const double rr = hypot(hprev, hk1);
-          double c = 0.0, sg = 0.0;
-          if (rr > 0.0) { c = hprev / rr; sg = hk1 / rr; }
-          const double ghn = -sg * ghk;
-          if (b == 0) {
-            Rc[kk] = rr;
-            A.cs[kk] = c;
-            A.sn[kk] = sg;
-            A.gh[kk] = c * ghk;
-            A.gh[kk + 1] = ghn;
+          if (lane == 0) {
+            const double hprev = carry;
+            const double rr = hypot(hprev, hk1);
+            double c = 0.0, sg = 0.0;
+            if (rr > 0.0) { c = hprev / rr; sg = hk1 / rr; }
+            const double ghn = -sg * ghk;
+            if (b == 0) {
+              Rc[kk] = rr;
+              A.cs[kk] = c;
+              A.sn[kk] = sg;
+              A.gh[kk] = c * ghk;
+              A.gh[kk + 1] = ghn;
+            }
+            s_rot[0] = ghn;
+            s_rot[1] = rr;
           }
-          s_rot[0] = ghn;
-          s_rot[1] = rr;
         }
         __syncthreads();
         const double ghn = s_rot[0], rr = s_rot[1];
@@ -1216,7 +1289,7 @@ void *kernel_for(int method, int f32) {
 
 // dynamic shared memory per CTA: the opt-in maximum (227 KB) minus room for
 // the kernels' static shared memory
-constexpr size_t SMEM_LIMIT = 227 * 1024 - 2048;
+constexpr size_t SMEM_LIMIT = 227 * 1024 - 4096;
 
 // Function attributes of a kernel variant, set once per process: the largest
 // dynamic shared memory any launch may request and non-portable cluster sizes.
