@@ -153,9 +153,11 @@ typedef struct lpk_stats {
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.
- *  LPK_EXEC_AUTO:    one thread-block cluster (hardware cluster barrier, u in
- *                    distributed shared memory) when u fits in 16 CTAs' shared
- *                    memory, else the grid path.
+ *  LPK_EXEC_AUTO:    on the first Krylov solve of each problem, a few
+ *                    iterations of every path (grid; clusters of 16, 8, 4)
+ *                    are timed on the actual system and the fastest is kept
+ *                    for that problem (for AB-GMRES only the clusters, unless
+ *                    none can hold the problem).
  *  LPK_EXEC_GRID:    every SM, software grid barrier, u in global memory.
  *  LPK_EXEC_CLUSTER: the cluster path (LPK_INVALID_ARG at solve time if u does
  *                    not fit).
@@ -286,7 +288,11 @@ LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, c
  * (one host thread and CUDA stream per LP) with its persistent Krylov kernel
  * on a thread-block cluster of its own; contexts in LPK_EXEC_AUTO mode take
  * the LPK_EXEC_BATCH path for these solves, so every LP gives bitwise the
- * result it gives when solved alone on that path.
+ * result it gives when solved alone on that path.  With more than 8 LPs at
+ * once, set the environment variable CUDA_DEVICE_MAX_CONNECTIONS to 32 before
+ * the process creates its CUDA context: with the default of 8 hardware work
+ * queues, streams share queues and one LP's persistent kernel holds back the
+ * launches of another (measured: 2.7 vs 6.4 LPs/s for 16 assignment LPs).
  * ------------------------------------------------------------------------ */
 
 /* Solve `count` LPs at once: LP i is problems[i] with b[i], c[i] (lengths as

@@ -897,12 +897,24 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
             __syncthreads();
           }
           if (!Gp.sync(&s_ok)) return;
-          // h_i = sum of the G partials in CTA order, spread over all threads
-          for (int i = tid; i <= kk; i += NT) {
-            double acc = 0.0;
+          // h_i = sum of the G partials in CTA order: a thread per i for a
+          // cluster (G <= 16), a warp per i (lanes over CTAs, fixed shuffle
+          // order) for the grid, where G is the number of SMs
+          if (G <= 32) {
+            for (int i = tid; i <= kk; i += NT) {
+              double acc = 0.0;
 #pragma unroll 8
-            for (int t = 0; t < G; ++t) acc += ldcg(A.gpart + (size_t)t * ld + i);
-            h[i] = acc;
+              for (int t = 0; t < G; ++t) acc += ldcg(A.gpart + (size_t)t * ld + i);
+              h[i] = acc;
+            }
+          } else {
+            const int gw = b * KWPB + wi, GW = G * KWPB;
+            for (int i = gw; i <= kk; i += GW) {
+              double acc = 0.0;
+              for (int t = lane; t < G; t += 32) acc += ldcg(A.gpart + (size_t)t * ld + i);
+              acc = warp_sum(acc);
+              if (lane == 0) h[i] = acc;
+            }
           }
           if (!Gp.sync(&s_ok)) return;
           // w -= V h on this CTA's rows: a warp per four rows at a time, lanes
@@ -1555,11 +1567,16 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
 // (each with the shared-memory row cache when it fits).
 lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
   const int cands[4][2] = {{1, 0}, {2, 16}, {2, 8}, {2, 4}};
+  // AB-GMRES: the cost of the grid path grows with the basis (reductions over
+  // every SM's partials), which a probe of a few iterations does not see; the
+  // grid is taken only when no cluster can hold the problem
+  const bool abg = base.method == M_ABG;
   const int save_mode = ctx->cluster_mode, save_cs = ctx->cluster_size_override;
   const lpk_stats save_stats = ctx->stats;
   double best = 1e300;
   int bm = 1, bcs = 0;
   for (int i = 0; i < 4; ++i) {
+    if (abg && i == 0) continue;
     ctx->cluster_mode = cands[i][0];
     ctx->cluster_size_override = cands[i][1];
     KArgs A = base;
