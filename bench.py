@@ -146,6 +146,28 @@ def algorithmic_bytes(stats, m, n, nnz, precision):
             + stats.get("basis_passes", 0) * 8 * m)
 
 
+def replica_offsets(rank, batch):
+    """Seed offsets of the LPs rank `rank` solves: replicas are independent
+    units (weak scaling), every rank gets its own LPs of the family."""
+    return [rank * batch + i for i in range(batch)]
+
+
+def max_over_ranks(value, dist, device=None):
+    """The largest value over all ranks (the job's time); the value itself
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_throughput(world, batch, steps, total_ms):
+    """Whole-job LPs/s: every rank solved batch x steps LPs in at most total_ms."""
+    return world * batch * steps / (total_ms / 1e3)
+
+
 def percentile(vals, q):
     v = sorted(vals)
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
@@ -337,7 +359,7 @@ def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
     B = args.batch if args.batch > 0 else wl["batch"]
     prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
     # replicas: rank r solves its own LPs of the same family (weak scaling)
-    lps = [make_lp(args.workload, seed_offset=rank * B + i) for i in range(B)]
+    lps = [make_lp(args.workload, seed_offset=o) for o in replica_offsets(rank, B)]
     main_stream = torch.cuda.current_stream(dev)
     streams = [main_stream] if B == 1 else [torch.cuda.Stream(dev) for _ in range(B)]
     ctxs = [lpk.Context(local, st.cuda_stream) for st in streams]
@@ -373,12 +395,8 @@ def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
                 lat_ms.append(r[3]["solve_ms"])
                 infos.append(r[3])
     stats = sum_stats(ctxs)
-    total_ms = sum(step_ms)
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    lps_per_s = world * B * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
+    lps_per_s = weak_throughput(world, B, args.steps, total_ms)
     worst = max(infos, key=lambda d: (d["status"] != 0, d["rel_gap"]))
 
     # plain FP64, one LP at a time, on the autotuned single-LP path
