@@ -42,7 +42,7 @@ class Options(C.Structure):
                 ("start_tol", C.c_double), ("backtrack", C.c_double),
                 ("max_ipm", C.c_int32), ("max_krylov", C.c_int32), ("inner_sweeps", C.c_int32),
                 ("method", C.c_int32), ("color_seed", C.c_uint64), ("verbose", C.c_int32),
-                ("pad", C.c_int32)]
+                ("corrector_ba", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -87,6 +87,14 @@ def lib():
         _lib.orc_ne_solve.restype = C.c_int32
         _lib.orc_ne_solve.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, C.c_int32,
                                       C.c_double, C.c_int32, C.c_double, C.c_int32, P, P, P]
+        _lib.orc_nrsor.restype = None
+        _lib.orc_nrsor.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, P]
+        _lib.orc_ls_krylov.restype = C.c_int32
+        _lib.orc_ls_krylov.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double,
+                                       C.c_double, C.c_int32, P, P, P]
+        _lib.orc_ls_solve.restype = C.c_int32
+        _lib.orc_ls_solve.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, C.c_int32, C.c_double,
+                                      C.c_double, C.c_int32, P, P, P]
         _lib.orc_default_options.restype = None
         _lib.orc_default_options.argtypes = [P]
         _lib.orc_lp_solve.restype = C.c_int32
@@ -144,6 +152,42 @@ def nesor(m, n, row_ptr, col_idx, a, perm, g, ell=1, omega=1.0):
     y = np.empty(m, np.float64)
     lib().orc_nesor(m, n, *[_p(x) for x in args], ell, omega, _p(z), _p(y))
     return z, y
+
+
+def nrsor(m, n, row_ptr, col_idx, a, perm, c, ell=1, omega=1.0):
+    """NR-SOR for min ||A^T y - c||: returns y[m] = B c."""
+    args = [_c(row_ptr, np.int64), _c(col_idx, np.int32), _c(a, np.float64), _c(perm, np.int32),
+            _c(c, np.float64)]
+    y = np.empty(m, np.float64)
+    lib().orc_nrsor(m, n, *[_p(x) for x in args], ell, omega, _p(y))
+    return y
+
+
+def ls_krylov(m, n, row_ptr, col_idx, a, perm, r, ell=1, omega=1.0, tol=1e-10, maxit=None):
+    """BA-GMRES (NR-SOR) on min ||A^T dy - r|| for a scaled A: (dw[n], dy[m], info)."""
+    maxit = m if maxit is None else maxit
+    args = [_c(row_ptr, np.int64), _c(col_idx, np.int32), _c(a, np.float64), _c(perm, np.int32),
+            _c(r, np.float64)]
+    dw = np.empty(n, np.float64)
+    dy = np.empty(m, np.float64)
+    info = KrylovInfo()
+    lib().orc_ls_krylov(m, n, *[_p(x) for x in args], ell, omega, tol, maxit, _p(dw), _p(dy),
+                        C.byref(info))
+    return dw, dy, info.as_dict()
+
+
+def ls_solve(m, n, row_ptr, col_idx, val, perm, d2, r, ell=1, omega=1.0, tol=1e-10, maxit=None):
+    """Corrector least squares min ||diag(sqrt d2) A^T dy - r|| by BA-GMRES:
+    (dy[m], dw[n], info)."""
+    maxit = m if maxit is None else maxit
+    args = [_c(row_ptr, np.int64), _c(col_idx, np.int32), _c(val, np.float64), _c(perm, np.int32),
+            _c(d2, np.float64), _c(r, np.float64)]
+    dy = np.empty(m, np.float64)
+    dw = np.empty(n, np.float64)
+    info = KrylovInfo()
+    lib().orc_ls_solve(m, n, *[_p(x) for x in args], ell, omega, tol, maxit, _p(dy), _p(dw),
+                       C.byref(info))
+    return dy, dw, info.as_dict()
 
 
 def krylov(method, m, n, row_ptr, col_idx, a, perm, f, ell=1, omega=1.0, tol=1e-10, maxit=None,

@@ -12,6 +12,9 @@
  *   Algorithm 3     MRNE preconditioned by inner its   -> mrne_core
  *   Algorithm 4     AB-GMRES preconditioned by NE-SOR  -> abgmres_core
  *   Sec. 2.2        w-form of the normal equations     -> orc_ne_solve
+ *   Sec. 3.2        BA-GMRES for the corrector stage,  -> orc_ls_solve, bagmres_core
+ *                   least-squares form (eq. ba_ne), NR-SOR inner iterations
+ *                                                      -> orc_nrsor
  *   Algorithm 1     Mehrotra predictor-corrector,      -> orc_lp_solve
  *                   Eq. (steplength), sigma rule, Gamma (Eq. errorMeasureDef),
  *                   centrality backtracking, eps_in schedule of Sec. 4.2
@@ -195,6 +198,33 @@ void orc_nesor(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_
      y accumulates d_i so that z = A^T y (used to recover dy without a product) */
   for (int32_t k = 0; k < ell; ++k)
     for (int32_t p = 0; p < m; ++p) ssor_row(perm[p], row_ptr, col_idx, a, nr2, g, omega, y, z);
+  free(nr2);
+}
+
+/* NR-SOR: the SOR method for the normal equations of the first kind
+   A A^T y = A c, i.e. for min ||A^T y - c|| (the columns of A^T are the rows
+   of A), ell forward sweeps from y = 0 with the residual r = c - A^T y kept
+   explicitly: d_i = omega (alpha_i, r) / ||alpha_i||^2, y_i += d_i,
+   r -= d_i alpha_i.  Returns y = B c, the inner-iteration left preconditioner
+   of BA-GMRES. */
+void orc_nrsor(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+               const double *a, const int32_t *perm, const double *c, int32_t ell, double omega,
+               double *y) {
+  double *nr2 = row_norms2(m, row_ptr, a);
+  double *r = dalloc(n);
+  memcpy(r, c, sizeof(double) * (size_t)n);
+  for (int32_t i = 0; i < m; ++i) y[i] = 0.0;
+  for (int32_t k = 0; k < ell; ++k)
+    for (int32_t p = 0; p < m; ++p) {
+      int32_t i = perm[p];
+      if (nr2[i] == 0.0) continue;
+      double t = 0.0;
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) t += a[q] * r[col_idx[q]];
+      double d = omega * t / nr2[i];
+      y[i] += d;
+      for (int64_t q = row_ptr[i]; q < row_ptr[i + 1]; ++q) r[col_idx[q]] -= d * a[q];
+    }
+  free(r);
   free(nr2);
 }
 
@@ -459,6 +489,146 @@ int32_t orc_ne_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t
   return 0;
 }
 
+/* BA-GMRES (left-preconditioned GMRES) on min ||A^T y - r0||: GMRES applied
+   to B A^T y = B r0 with B = NR-SOR, in m-space, from y = 0 (the caller
+   passes r0 = the residual of its current iterate), modified Gram-Schmidt and
+   Givens rotations as in Algorithm 4.  Stops when the preconditioned residual
+   estimate |g_{k+1}| <= ratio * ||B r0||.  Adds V_k p_k to y. */
+static int bagmres_core(const sys_t *S, const double *r0, double ratio, int32_t maxit, double *y,
+                        int32_t *iters) {
+  int32_t m = S->m, n = S->n;
+  int32_t cap = 16;
+  double *V = (double *)malloc(sizeof(double) * (size_t)m * (size_t)(cap + 1));
+  double *H = (double *)calloc((size_t)(cap + 1) * (size_t)cap, sizeof(double));
+  double *cs = dalloc(cap), *sn = dalloc(cap), *gh = dalloc(cap + 1);
+  double *w = dalloc(m), *t = dalloc(n);
+  orc_nrsor(m, n, S->rp, S->ci, S->a, S->perm, r0, S->ell, S->omega, w);   /* B r0 */
+  double beta = nrm2(m, w);
+  int rc = EXIT_MAXIT;
+  int32_t k = 0;
+  if (beta == 0.0) { rc = EXIT_CONVERGED; goto done; }
+  for (int32_t i = 0; i < m; ++i) V[i] = w[i] / beta;
+  gh[0] = beta;
+  double target = ratio * beta, res = beta;
+  while (1) {
+    if (res <= target) { rc = EXIT_CONVERGED; break; }
+    if (k >= maxit) { rc = EXIT_MAXIT; break; }
+    if (k + 1 > cap) {
+      int32_t nc = cap * 2;
+      double *V2 = (double *)realloc(V, sizeof(double) * (size_t)m * (size_t)(nc + 1));
+      double *H2 = (double *)calloc((size_t)(nc + 1) * (size_t)nc, sizeof(double));
+      for (int32_t j = 0; j < cap; ++j)
+        for (int32_t i = 0; i <= cap; ++i) H2[i + (size_t)j * (nc + 1)] = H[i + (size_t)j * (cap + 1)];
+      free(H);
+      V = V2; H = H2;
+      cs = (double *)realloc(cs, sizeof(double) * (size_t)nc);
+      sn = (double *)realloc(sn, sizeof(double) * (size_t)nc);
+      gh = (double *)realloc(gh, sizeof(double) * (size_t)(nc + 1));
+      cap = nc;
+    }
+    double *vk = V + (size_t)k * m;
+    spmv_t(m, n, S->rp, S->ci, S->a, vk, t);                                /* A^T v_k */
+    orc_nrsor(m, n, S->rp, S->ci, S->a, S->perm, t, S->ell, S->omega, w);  /* w = B A^T v_k */
+    double *hk = H + (size_t)k * (cap + 1);
+    for (int32_t i = 0; i <= k; ++i) {
+      double *vi = V + (size_t)i * m;
+      hk[i] = dot(m, w, vi);
+      axpy(m, -hk[i], vi, w);
+    }
+    hk[k + 1] = nrm2(m, w);
+    double hnext = hk[k + 1];
+    for (int32_t i = 0; i < k; ++i) {
+      double a = hk[i], b = hk[i + 1];
+      hk[i] = cs[i] * a + sn[i] * b;
+      hk[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    double rr = hypot(hk[k], hk[k + 1]);
+    if (!(rr > 0.0) || !isfinite(rr)) { rc = EXIT_BREAKDOWN; break; }
+    cs[k] = hk[k] / rr;
+    sn[k] = hk[k + 1] / rr;
+    hk[k] = rr;
+    hk[k + 1] = 0.0;
+    gh[k + 1] = -sn[k] * gh[k];
+    gh[k] = cs[k] * gh[k];
+    res = fabs(gh[k + 1]);
+    ++k;
+    if (hnext == 0.0) { rc = EXIT_CONVERGED; break; }
+    double *vn = V + (size_t)k * m;
+    for (int32_t i = 0; i < m; ++i) vn[i] = w[i] / hnext;
+  }
+  if (k > 0) {
+    double *pk = dalloc(k);
+    for (int32_t i = k - 1; i >= 0; --i) {
+      double sacc = gh[i];
+      for (int32_t j = i + 1; j < k; ++j) sacc -= H[i + (size_t)j * (cap + 1)] * pk[j];
+      pk[i] = sacc / H[i + (size_t)i * (cap + 1)];
+    }
+    for (int32_t j = 0; j < k; ++j) axpy(m, pk[j], V + (size_t)j * m, y);   /* y += V_k p_k */
+    free(pk);
+  }
+done:
+  *iters = k;
+  free(V); free(H); free(cs); free(sn); free(gh); free(w); free(t);
+  return rc;
+}
+
+int32_t orc_ls_krylov(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *a, const int32_t *perm, const double *r, int32_t ell,
+                      double omega, double tol, int32_t maxit, double *dw, double *dy,
+                      orc_krylov_info *info) {
+  sys_t S = {m, n, row_ptr, col_idx, a, perm, ell, omega};
+  double *f = dalloc(m), *c = dalloc(n), *g = dalloc(m);
+  /* the equivalent normal equations A A^T dy = A r: f = A r, and the explicit
+     residual ||f - A dw|| with dw = A^T dy, as for the other solvers */
+  spmv(m, row_ptr, col_idx, a, r, f);
+  double res0 = nrm2(m, f), target = tol * res0;
+  memset(info, 0, sizeof(*info));
+  info->res0 = res0;
+  for (int32_t i = 0; i < m; ++i) dy[i] = 0.0;
+  for (int32_t j = 0; j < n; ++j) dw[j] = 0.0;
+  double res = res0;
+  int32_t used = 0;
+  int rc = EXIT_CONVERGED;
+  /* reading (as for the other solvers): the recurrence ends the iteration, the
+     explicit residual decides convergence, at most ORC_MAX_RESTARTS restarts
+     from the current iterate.  The preconditioned residual must shrink by the
+     factor the explicit residual still has to shrink. */
+  for (int32_t rs = 0; rs <= ORC_MAX_RESTARTS; ++rs) {
+    if (res <= target) { rc = EXIT_CONVERGED; break; }
+    if (used >= maxit) { rc = EXIT_MAXIT; break; }
+    for (int32_t j = 0; j < n; ++j) c[j] = r[j] - dw[j];      /* residual of the LS problem */
+    int32_t it = 0;
+    rc = bagmres_core(&S, c, target / res, maxit - used, dy, &it);
+    used += it;
+    spmv_t(m, n, row_ptr, col_idx, a, dy, dw);                /* dw = A^T dy */
+    spmv(m, row_ptr, col_idx, a, dw, g);
+    for (int32_t i = 0; i < m; ++i) g[i] = f[i] - g[i];
+    res = nrm2(m, g);
+    if (rc != EXIT_CONVERGED) break;
+    if (res > target && rs < ORC_MAX_RESTARTS) info->restarts++;
+  }
+  info->iters = used;
+  info->res = res;
+  info->converged = res <= target;
+  info->breakdown = rc == EXIT_BREAKDOWN;
+  free(f); free(c); free(g);
+  return 0;
+}
+
+int32_t orc_ls_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     const double *val, const int32_t *perm, const double *d2, const double *r,
+                     int32_t ell, double omega, double tol, int32_t maxit, double *dy, double *dw,
+                     orc_krylov_info *info) {
+  int64_t nnz = row_ptr[m];
+  double *ahat = dalloc(nnz), *rho = dalloc(m), *dyh = dalloc(m);
+  orc_scale_rows(m, row_ptr, col_idx, val, d2, ahat, rho);
+  /* A D = D_cal A_hat, so (A D)^T dy = A_hat^T (D_cal dy): solve for dy_hat = D_cal dy */
+  orc_ls_krylov(m, n, row_ptr, col_idx, ahat, perm, r, ell, omega, tol, maxit, dw, dyh, info);
+  for (int32_t i = 0; i < m; ++i) dy[i] = rho[i] > 0.0 ? dyh[i] / rho[i] : 0.0;
+  free(ahat); free(rho); free(dyh);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: Mehrotra predictor-corrector with the w-recurrence            */
 /* ------------------------------------------------------------------------ */
@@ -477,6 +647,7 @@ void orc_default_options(orc_options *o) {
   o->inner_sweeps = 1;
   o->method = ORC_MRNE;
   o->color_seed = 0x5EEDULL;
+  o->corrector_ba = 0;
 }
 
 static double step_len(int32_t n, const double *x, const double *dx, double eta) {
@@ -602,8 +773,15 @@ static int32_t ipm_core(int32_t m, int32_t n, const int64_t *rp, const int32_t *
       /* corrector: f_cc = A S^-1 (dX_af ds_af - sigma mu e); reading: sigma * mu
          (the mu of this iterate) as in the equations that define f_cc */
       for (int32_t j = 0; j < n; ++j) h[j] = (dxa[j] * dsa[j] - sigma * mu) / s[j];
-      spmv(m, rp, ci, val, h, f);
-      orc_ne_solve(m, n, rp, ci, val, perm, d2, f, ell, om, meth, eps_in, maxit, dyc, dwc, &ki);
+      if (opt->corrector_ba) {
+        /* BA-GMRES on the least-squares form of the corrector (Sec. 3.2):
+           min ||(A D)^T dy - r||, r = (XS)^-1/2 (dX_af ds_af - sigma mu e) = h / d */
+        for (int32_t j = 0; j < n; ++j) tmpn[j] = h[j] / d[j];
+        orc_ls_solve(m, n, rp, ci, val, perm, d2, tmpn, ell, om, eps_in, maxit, dyc, dwc, &ki);
+      } else {
+        spmv(m, rp, ci, val, h, f);
+        orc_ne_solve(m, n, rp, ci, val, perm, d2, f, ell, om, meth, eps_in, maxit, dyc, dwc, &ki);
+      }
       info->krylov_iters_total += ki.iters;
       it_cc = ki.iters;
       if (!ki.converged) failed = 1;

@@ -50,7 +50,7 @@ typedef struct {
   int32_t method;      /* ORC_MRNE, ORC_CGNE, ORC_ABGMRES                     */
   uint64_t color_seed;
   int32_t verbose;     /* 1: one line per interior-point iteration on stderr */
-  int32_t pad;
+  int32_t corrector_ba;/* 1: corrector stage by BA-GMRES (NR-SOR), Sec. 3.2   */
 } orc_options;
 
 typedef struct {
@@ -116,6 +116,28 @@ int32_t orc_ne_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t
                      const double *val, const int32_t *perm, const double *d2, const double *f,
                      int32_t ell, double omega, int32_t method, double tol, int32_t maxit,
                      double *dy, double *dw, orc_krylov_info *info);
+
+/* NR-SOR inner iterations for min ||A^T y - c|| (A in CSR, rows = the columns
+ * of A^T, visited in the order perm): y[m] = B^<ell> c. */
+void orc_nrsor(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+               const double *a, const int32_t *perm, const double *c, int32_t ell, double omega,
+               double *y);
+
+/* BA-GMRES preconditioned by NR-SOR on min ||A^T dy - r|| for an already
+ * scaled A (the corrector stage in least-squares form, Sec. 3.2): dy[m],
+ * dw[n] = A^T dy.  info->res is the explicit ||A r - A dw||. */
+int32_t orc_ls_krylov(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      const double *a, const int32_t *perm, const double *r, int32_t ell,
+                      double omega, double tol, int32_t maxit, double *dw, double *dy,
+                      orc_krylov_info *info);
+
+/* The corrector-stage least-squares problem min ||diag(sqrt(d2)) A^T dy - r||
+ * through the row scaling of Sec. 3.5 and BA-GMRES; dw = diag(sqrt(d2)) A^T dy
+ * is the minimum-norm solution of A diag(sqrt(d2)) dw = A diag(sqrt(d2)) r. */
+int32_t orc_ls_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     const double *val, const int32_t *perm, const double *d2, const double *r,
+                     int32_t ell, double omega, double tol, int32_t maxit, double *dy, double *dw,
+                     orc_krylov_info *info);
 
 void orc_default_options(orc_options *o);
 

@@ -143,3 +143,15 @@ def test_oracle_is_deterministic(orc):
     r2 = orc.lp_solve_lp(lp)
     for a, b in zip(r1[:3], r2[:3]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("method", [0, 2])
+def test_tiny_lp_with_bagmres_corrector_matches_highs(orc, method):
+    # the corrector stage solved in least-squares form by BA-GMRES (Sec. 3.2)
+    lp = gen.tiny_lp()
+    x, y, s, info = orc.lp_solve_lp(lp, method=method, inner_sweeps=1 if method < 2 else 2,
+                                    corrector_ba=1)
+    assert info["status_name"] == "OK"
+    ref = highs(lp)
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
+    assert certificates_ok(lp, x, y, s)

@@ -300,3 +300,50 @@ def test_w_recurrence_solves_the_newton_system(orc):
     assert np.allclose(A @ dx2, 0, atol=1e-9)
     assert np.allclose(A.T @ dy2 + ds2, 0, atol=1e-10)
     assert np.allclose(s * dx2 + x * ds2, -dx * ds + smu, atol=1e-10)
+
+
+# ---------------------------------------------------------------- BA-GMRES (corrector, Sec. 3.2)
+@pytest.mark.parametrize("ell,omega", [(1, 1.0), (3, 1.2)])
+def test_nrsor_equals_sor_on_first_kind_normal_equations(orc, ell, omega):
+    # NR-SOR for min ||A^T y - c|| is SOR on A A^T y = A c (written densely in
+    # splitting form) from y = 0
+    lp = small_lp(m=15, n=40, density=0.25, seed=5)
+    nc, color, perm, cptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 13)
+    c = np.random.default_rng(4).standard_normal(lp.n)
+    y = orc.nrsor(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, c, ell, omega)
+    _, y2 = splitting_sor(dense(lp), perm, dense(lp) @ c, ell, omega)
+    assert np.allclose(y, y2, rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("rank_deficient", [False, True])
+def test_bagmres_least_squares_solution(orc, rank_deficient):
+    # min ||A^T dy - r||: dw = A^T dy is the projection of r onto R(A^T), unique
+    # also when A A^T is singular
+    lp = gen.medium_lp(scale=0.004, seed=21) if rank_deficient else small_lp(m=20, n=50, density=0.2, seed=9)
+    ahat, Ah = scaled_system(orc, lp, seed=5)
+    nc, color, perm, cptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 3)
+    r = np.random.default_rng(6).standard_normal(lp.n)
+    dw, dy, info = orc.ls_krylov(lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, r, 2, 1.0, 1e-12, 2000)
+    assert info["converged"] and not info["breakdown"]
+    ref = Ah.T @ np.linalg.lstsq(Ah.T, r, rcond=None)[0]
+    assert np.allclose(dw, ref, atol=1e-8 * np.linalg.norm(ref))
+    assert np.allclose(dw, Ah.T @ dy, atol=1e-12 * np.linalg.norm(dw))
+    # the normal equations of the first kind hold for dy
+    assert np.linalg.norm(Ah @ (Ah.T @ dy) - Ah @ r) <= 1e-11 * np.linalg.norm(Ah @ r)
+
+
+def test_ls_solve_gives_the_min_norm_direction_of_ne_solve(orc):
+    # the corrector in least-squares form (BA-GMRES) and in w-form (MRNE) give
+    # the same minimum-norm dw for f = A D r
+    lp = small_lp(m=20, n=50, density=0.2, seed=12)
+    nc, color, perm, cptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 4)
+    rng = np.random.default_rng(7)
+    d2 = np.exp(rng.uniform(-3, 3, lp.n))
+    r = rng.standard_normal(lp.n)
+    dy, dw, info = orc.ls_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, r, 2, 1.0, 1e-12, 500)
+    f = dense(lp) @ (np.sqrt(d2) * r)
+    dy2, dw2, info2 = orc.ne_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, f, 1, 1.0, 0,
+                                   1e-12, 500)
+    assert info["converged"] and info2["converged"]
+    assert np.allclose(dw, dw2, atol=1e-8 * np.linalg.norm(dw))
+    assert np.allclose(dw, np.sqrt(d2) * (dense(lp).T @ dy), atol=1e-10 * np.linalg.norm(dw))
