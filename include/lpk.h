@@ -102,6 +102,9 @@ typedef struct lpk_options {
   int32_t precision;  /* lpk_precision */
   int32_t verbose;    /* 1: one line per interior-point iteration on stderr */
   uint64_t color_seed;
+  int32_t corrector;  /* 0: corrector stage by `solver`; 1: by BA-GMRES with
+                         NR-SOR on its least-squares form (Sec. 3.2)       */
+  int32_t reserved;
 } lpk_options;
 
 /* Result summary of lpk_lp_solve.  gamma is the error measure of
@@ -278,6 +281,21 @@ LPK_API lpk_status lpk_ne_solve_noalloc(lpk_ctx *ctx, lpk_problem *P, const doub
 /* Interior-point solve (Algorithm 1 with the w-recurrence of Sec. 2.2): b[m],
  * c[n] in; x[n], y[m], s[n] out.  opt may be NULL (defaults).  info may be
  * NULL.  Returns LPK_OK when Gamma <= tol and rel_gap <= tol. */
+/* The corrector stage in least-squares form (Sec. 3.2, Eq. ba_ne):
+ * min || diag(sqrt(d2)) A^T dy - r ||, i.e. the normal equations of the first
+ * kind A diag(d2) A^T dy = A diag(sqrt(d2)) r, solved in m-space by BA-GMRES
+ * (left-preconditioned GMRES) with NR-SOR inner iterations on the row-scaled
+ * matrix of Sec. 3.5.  d2[n] > 0 and r[n] in; dy[m] and dw[n] =
+ * diag(sqrt(d2)) A^T dy out (dw, the minimum-norm solution of
+ * A diag(sqrt(d2)) dw = A diag(sqrt(d2)) r, may be NULL).  Convergence: the
+ * explicit scaled residual ||f_hat - A_hat dw|| <= tol ||f_hat|| with
+ * f_hat = A_hat r (kinfo->converged).  inner_sweeps = NR-SOR sweeps per
+ * application, max_iter 0 -> m.  Layout and staging as lpk_ne_solve. */
+LPK_API lpk_status lpk_ls_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *r,
+                                int32_t inner_sweeps, double omega, int32_t precision, double tol,
+                                int32_t max_iter, double *dy, double *dw, lpk_krylov_info *kinfo,
+                                int32_t on_device);
+
 LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, const double *c,
                                 const lpk_options *opt, double *x, double *y, double *s,
                                 lpk_info *info, int32_t on_device);

@@ -391,6 +391,62 @@ LPK_API lpk_status lpk_ne_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, 
   return LPK_OK;
 }
 
+namespace {
+__global__ void k_sqrt_mul(int n, const double *d2, const double *r, double *out) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) out[j] = sqrt(d2[j]) * r[j];
+}
+}  // namespace
+
+LPK_API lpk_status lpk_ls_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *r,
+                                int32_t inner_sweeps, double omega, int32_t precision, double tol,
+                                int32_t max_iter, double *dy, double *dw, lpk_krylov_info *kinfo,
+                                int32_t on_device) {
+  CHECK_CTX(ctx);
+  CHECK_P(ctx, P);
+  DevProblem &d = P->d;
+  if (!d2 || !r || !dy || inner_sweeps < 1 || !(omega > 0.0 && omega < 2.0) || !(tol >= 0.0) ||
+      max_iter < 0 || (precision != LPK_FP64 && precision != LPK_MIXED)) {
+    ctx->err = "lpk_ls_solve: invalid arguments";
+    return LPK_INVALID_ARG;
+  }
+  Vec vd2(ctx, d2, d.n_in, on_device, false), vr(ctx, r, d.n_in, on_device, false),
+      vdy(ctx, dy, d.m_in, on_device, true), vdw(ctx, dw, d.n_in, on_device, true);
+  TRY(vd2.init());
+  TRY(vr.init());
+  TRY(vdy.init());
+  TRY(vdw.init());
+  DevBuf t(ctx);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &t.p, 3 * d.m + 4 * d.n + 7));
+  double *td2 = t.p, *tr = td2 + d.n + 1, *tt = tr + d.n + 1, *tf = tt + d.n + 1, *tdy = tf + d.m + 1,
+         *tdw = tdy + d.m + 1, *tmp = tdw + d.n + 1;
+  gather_n(ctx, d, vd2.dev, td2);
+  TRY(check_d2(ctx, d, td2));
+  gather_n(ctx, d, vr.dev, tr);
+  scale_rows(ctx, d, td2);
+  // f = A D r, the right-hand side of the equivalent normal equations
+  if (d.n > 0) LPK_LAUNCH(ctx, k_sqrt_mul, (d.n + 255) / 256, 256, 0, ctx->stream, d.n, td2, tr, tt);
+  spmv_csr(ctx, d, tt, tf, nullptr, 1.0);
+  KrylovResult kr;
+  const int maxit = max_iter > 0 ? max_iter : d.m;
+  TRY(ls_solve_scaled(ctx, d, tr, tf, inner_sweeps, omega, precision, tol, maxit, tdy, tdw, tmp, &kr));
+  scatter_m(ctx, d, tdy, vdy.dev);
+  if (dw) scatter_n(ctx, d, tdw, vdw.dev, nullptr);
+  LPK_CUDA_TRY(ctx, cudaGetLastError());
+  TRY(vdy.finish());
+  TRY(vdw.finish());
+  LPK_CUDA_TRY(ctx, ctx_sync(ctx));
+  if (kinfo) {
+    kinfo->iters = kr.iters;
+    kinfo->converged = kr.converged;
+    kinfo->restarts = kr.restarts;
+    kinfo->breakdown = kr.breakdown;
+    kinfo->res0 = kr.res0;
+    kinfo->res = kr.res;
+  }
+  return LPK_OK;
+}
+
 LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, const double *c,
                                 const lpk_options *opt, double *x, double *y, double *s, lpk_info *info,
                                 int32_t on_device) {
@@ -403,6 +459,7 @@ LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, c
   if (!b || !c || !x || !y || !s || o.inner_sweeps < 1 || !(o.omega > 0.0 && o.omega < 2.0) ||
       !(o.eta > 0.0 && o.eta < 1.0) || o.max_ipm < 0 || o.max_krylov < 0 ||
       (o.solver != LPK_MRNE && o.solver != LPK_CGNE && o.solver != LPK_ABGMRES) ||
+      (o.corrector != 0 && o.corrector != 1) ||
       (o.precision != LPK_FP64 && o.precision != LPK_MIXED)) {
     ctx->err = "lpk_lp_solve: invalid arguments";
     return LPK_INVALID_ARG;

@@ -233,6 +233,23 @@ lpk_status ne_solve_scaled(lpk_ctx *ctx, DevProblem &P, const double *f, int ell
   return LPK_OK;
 }
 
+// The corrector stage in least-squares form (Sec. 3.2): min ||A_hat^T dy_hat - r||
+// by BA-GMRES with NR-SOR; f = A D r is its m-space image (f_hat = D_cal^-1 f
+// gives the explicit residual ||f_hat - A_hat dw|| used for convergence)
+lpk_status ls_solve_scaled(lpk_ctx *ctx, DevProblem &P, const double *r, const double *f, int ell, double omega,
+                           int precision, double tol, int maxit, double *dy, double *dw, double *tmp_m,
+                           KrylovResult *kr) {
+  cudaStream_t st = ctx->stream;
+  if (P.m > 0) LPK_LAUNCH(ctx, k_div, eb(P.m), TPB, 0, st, P.m, f, P.rho, tmp_m);
+  lpk_status rc = krylov_solve_ls(ctx, P, precision, ell, omega, r, tmp_m, tol, maxit, dw, dy, kr);
+  if (rc != LPK_OK) return rc;
+  if (ctx->verbose >= 2)
+    fprintf(stderr, "  ba-gmres: it=%d restarts=%d conv=%d brk=%d res/res0=%.3e (tol %.1e)\n", kr->iters,
+            kr->restarts, kr->converged, kr->breakdown, kr->res0 > 0 ? kr->res / kr->res0 : 0.0, tol);
+  if (P.m > 0) LPK_LAUNCH(ctx, k_div, eb(P.m), TPB, 0, st, P.m, dy, P.rho, dy);
+  return LPK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
@@ -391,8 +408,15 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
       }
       if (n > 0) LPK_LAUNCH(ctx, k_h, eb(n), TPB, 0, st, n, dxa, dsa, s, sigma * mu, hh);
       spmv_csr(ctx, P, hh, f, nullptr, 1.0);  // f_cc = A h
-      if ((rc = ne_solve_scaled(ctx, P, f, ell, om, solver, prec, eps_in, maxit, dyc, dwc, tm2, &kr)) != LPK_OK)
+      if (o.corrector == 1) {
+        // least-squares form solved by BA-GMRES (Sec. 3.2): r = (XS)^-1/2 (dX ds - sigma mu e) = h / d
+        if (n > 0) LPK_LAUNCH(ctx, k_div, eb(n), TPB, 0, st, n, hh, d, tn3);
+        if ((rc = ls_solve_scaled(ctx, P, tn3, f, ell, om, prec, eps_in, maxit, dyc, dwc, tm2, &kr)) != LPK_OK)
+          return rc;
+      } else if ((rc = ne_solve_scaled(ctx, P, f, ell, om, solver, prec, eps_in, maxit, dyc, dwc, tm2, &kr)) !=
+                 LPK_OK) {
         return rc;
+      }
       info.krylov_iters_total += kr.iters;
       it_cc = kr.iters;
       if (!kr.converged) failed = true;

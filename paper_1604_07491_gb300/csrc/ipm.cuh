@@ -5,6 +5,9 @@
 // Krylov solve of the row-scaled system for right-hand side f (sweep order);
 // scale_rows must have been called for the current d2.  dy (m, sweep order)
 // and dw (n) are unscaled outputs; tmp_m is an m-vector of scratch.
+lpk_status ls_solve_scaled(lpk_ctx *ctx, DevProblem &P, const double *r, const double *f, int ell, double omega,
+                           int precision, double tol, int maxit, double *dy, double *dw, double *tmp_m,
+                           KrylovResult *kr);
 lpk_status ne_solve_scaled(lpk_ctx *ctx, DevProblem &P, const double *f, int ell, double omega, int solver,
                            int precision, double tol, int maxit, double *dy, double *dw, double *tmp_m,
                            KrylovResult *kr);

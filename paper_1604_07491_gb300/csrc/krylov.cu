@@ -59,7 +59,7 @@ constexpr unsigned long long TIMEOUT_NS = 5000000000ull;  // 5 s per barrier wai
 constexpr int MAX_CLUSTER = 16;
 constexpr int MAX_SHIFT = 14;         // <= 2^14 doubles (128 KB) of u per CTA
 
-enum { M_MRNE = 0, M_CGNE = 1, M_ABG = 2, M_SWEEP = 7, M_SWEEP_SSOR = 8, M_SWEEP_SOR = 9 };
+enum { M_MRNE = 0, M_CGNE = 1, M_ABG = 2, M_BAG = 3, M_SWEEP = 7, M_SWEEP_SSOR = 8, M_SWEEP_SOR = 9 };
 enum { EXIT_CONV = 0, EXIT_MAXIT = 1, EXIT_BREAK = 2, EXIT_CYCLE = 3 };
 
 struct KrylovCtl {
@@ -108,6 +108,9 @@ struct KArgs {
   // [CTAs x ldv]
   double *V, *R, *cs, *sn, *gh, *h1, *h2, *pv, *wt, *gpart;
   int kmax, ldv;
+  // BA-GMRES (corrector stage in least-squares form): the n-space right-hand
+  // side r of min ||A_hat^T dy - r||; f = A_hat r holds the m-space image
+  const double *rn;
 };
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -652,6 +655,38 @@ __device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, co
   return acc;
 }
 
+// u = -A_hat^T x into the sweep state (u in global memory or in the
+// cluster's shared memory): the starting point of an NR-SOR sweep on
+// min ||A_hat^T y - A_hat^T x||, same column interleaving as csc_products
+template <typename GRP>
+__device__ __forceinline__ void csc_to_u(const GRP &Gp, const KArgs &A, const double *x) {
+  constexpr int CW = 4;
+  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
+  for (int j0 = tid; j0 < A.n; j0 += CW * NT) {
+    int q0[CW], q1[CW];
+    double sv[CW];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int j = j0 + u * NT;
+      q0[u] = j < A.n ? __ldg(A.cp + j) : 0;
+      q1[u] = j < A.n ? __ldg(A.cp + j + 1) : 0;
+      len = max(len, q1[u] - q0[u]);
+      sv[u] = 0.0;
+    }
+    for (int t = 0; t < len; ++t) {
+#pragma unroll
+      for (int u = 0; u < CW; ++u) {
+        const int q = q0[u] + t;
+        if (q < q1[u]) sv[u] += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CW; ++u)
+      if (j0 + u * NT < A.n) Gp.ust(j0 + u * NT, -sv[u]);
+  }
+}
+
 template <typename GRP>
 __device__ __forceinline__ GRP make_group(const KArgs &A);
 template <>
@@ -822,8 +857,14 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         gnorm = sqrt(w[1]);
         if (A.hist && cta0) A.hist[k] = gnorm;
       }
-    } else if (METH == M_ABG) {
+    } else if (METH == M_ABG || METH == M_BAG) {
       // ---- Algorithm 4: AB-GMRES with NE-SOR inner iterations ----------------
+      // ---- and BA-GMRES with NR-SOR (corrector in least-squares form) ---------
+      // BA-GMRES (Sec. 3.2) runs GMRES on B A_hat^T dy = B r in m-space, B the
+      // NR-SOR inner iterations for min ||A_hat^T y - c||.  NR-SOR is the row
+      // sweep of NE-SOR with g = 0 started from u = -c (then u = -(residual)
+      // and d_i = omega (alpha_i, c - A_hat^T y)), so both methods share the
+      // sweep, the basis, the orthogonalisation and the rotations.
       // V is row-major [m x ldv]: row r holds (v_0)_r, (v_1)_r, ..., so both the
       // dot products (threads over basis vectors) and the updates (a warp over
       // one row's coefficients) read contiguous memory.  Orthogonalisation is
@@ -837,17 +878,52 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       const int RB = (m + G - 1) / G, rlo = min(m, b * RB), rhi = min(m, rlo + RB);
       const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
       const size_t ld = (size_t)A.ldv;
+      constexpr bool BA = METH == M_BAG;
       double ghk = gnorm;          // rotated right-hand side entry of the newest row
-      double hs = gnorm;           // norm of the vector the next sweep runs on
+      double hs = gnorm;           // norm of the vector the next operator application takes
       const double *vin = A.g;     // that vector (unnormalised)
-      if (cta0) A.gh[0] = gnorm;
+      double tgt = target;         // stopping level of the recurrence estimate
+      if (BA) {
+        // start: z = B c, c = r - A_hat^T dy (dw holds A_hat^T dy), beta = ||z||;
+        // the preconditioned residual must shrink by the factor the explicit
+        // residual still has to shrink
+        for (int j = tid; j < n; j += NT) Gp.ust(j, -(ldcg(A.rn + j) - ldcg(A.dw + j)));
+        for (int i = tid; i < m; i += NT) A.qt[i] = 0.0;   // g = 0 of the NR-SOR sweeps
+        if (!Gp.sync(&s_ok)) return;
+        if (!inner_sweeps<TV>(A, Gp, &s_ok, A.qt, false, nullptr, Cn, Z)) return;
+        double v1[1] = {0.0};
+        for (int i = tid; i < m; i += NT) {
+          const double zi = ldcg(A.z + i);
+          v1[0] += zi * zi;
+        }
+        put_partials<1>(Gp, v1, A.part, sred);
+        if (!Gp.sync(&s_ok)) return;
+        get_sums<1>(Gp, v1, A.part, sred);
+        const double beta = sqrt(v1[0]);
+        tgt = gnorm > 0.0 ? target / gnorm * beta : 0.0;
+        ghk = hs = beta;
+        vin = A.z;
+      }
+      double est = ghk;            // |rotated rhs|: the residual estimate of the recurrence
+      if (cta0) A.gh[0] = ghk;
       int kk = 0;                  // basis vectors of this cycle
       __shared__ double s_rot[2];
       __shared__ double s_dot[KWPB][32];
       while (true) {
-        if (gnorm <= target) { reason = EXIT_CONV; break; }
+        if (est <= tgt) { reason = EXIT_CONV; break; }
         if (k >= A.maxit) { reason = EXIT_MAXIT; break; }
         if (kk >= A.kmax) { reason = EXIT_CYCLE; break; }
+        const double ihs = 1.0 / hs;
+        if (BA) {
+          // v_kk = vin / hs; w = B A_hat^T vin / hs (u = -A_hat^T vin, NR-SOR)
+          for (int r = rlo + threadIdx.x; r < rhi; r += blockDim.x) A.V[(size_t)r * ld + kk] = ldcg(vin + r) * ihs;
+          ++Cn.cols;
+          csc_to_u(Gp, A, vin);
+          if (!Gp.sync(&s_ok)) return;
+          if (!inner_sweeps<TV>(A, Gp, &s_ok, A.qt, false, nullptr, Cn, Z)) return;
+          for (int r = rlo + threadIdx.x; r < rhi; r += blockDim.x) A.wt[r] = ldcg(A.z + r) * ihs;
+          __syncthreads();
+        } else {
         // z_k = B v_k (u is zero here)
         if (!inner_sweeps<TV>(A, Gp, &s_ok, vin, false, nullptr, Cn, Z)) return;
         const double *uwv = A.uw;
@@ -858,7 +934,6 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         }
         // v_kk = vin / hs and w = A_hat u / hs on this CTA's rows
         ++Cn.rows;
-        const double ihs = 1.0 / hs;
         for (int r = rlo + wi; r < rhi; r += KWPB) {
           const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
           double sacc = 0.0;
@@ -873,6 +948,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           }
         }
         __syncthreads();
+        }
         double wn2 = 0.0;
         for (int pass = 0; pass < 2; ++pass) {
           double *h = pass == 0 ? A.h1 : A.h2;
@@ -1007,8 +1083,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         ghk = ghn;
         ++kk;
         ++k;
-        gnorm = fabs(ghn);
-        if (A.hist && cta0) A.hist[k] = gnorm;
+        est = fabs(ghn);
+        if (!BA) gnorm = est;
+        if (A.hist && cta0) A.hist[k] = est;
         if (hk1 == 0.0) { reason = EXIT_CONV; break; }  // lucky breakdown: exact
         vin = A.wt;
         hs = hk1;
@@ -1030,6 +1107,16 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         Gp.uzero(n);
         if (!Gp.sync(&s_ok)) return;
         Cn.basis += kk;
+        if (BA) {
+          // dy += V p on this CTA's rows (dw = A_hat^T dy follows below)
+          for (int r = rlo + wi; r < rhi; r += KWPB) {
+            double sacc = 0.0;
+            for (int i = lane; i < kk; i += 32) sacc += ldcg(A.pv + i) * ldcg(A.V + (size_t)r * ld + i);
+            sacc = warp_sum(sacc);
+            if (lane == 0) A.dy[r] = ldcg(A.dy + r) + sacc;
+          }
+          if (!Gp.sync(&s_ok)) return;
+        } else {
         // q = V p on this CTA's rows
         for (int r = rlo + wi; r < rhi; r += KWPB) {
           double sacc = 0.0;
@@ -1044,6 +1131,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           for (int j = tid; j < n; j += NT) A.dw[j] = ldcg(A.dw + j) + uget(j);
         for (int i = tid; i < m; i += NT) A.dy[i] = ldcg(A.dy + i) + zget(i);
         if (!Gp.sync(&s_ok)) return;
+        }
       }
     } else {  // CGNE
       // z0 = C g0, u0 = A^T z0, gamma0 = (g0, z0)
@@ -1143,7 +1231,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       }
     }
     // ---- explicit residual g = f - A_hat dw; restart when it disagrees ------
-    if (A.wy) {  // dw = A_hat^T dy in FP64 keeps the two spaces consistent
+    if (A.wy || METH == M_BAG) {  // dw = A_hat^T dy in FP64 keeps the two spaces consistent
       ++Cn.cols;
       csc_products(Gp, A, A.dy, A.dw);
       if (!Gp.sync(&s_ok)) return;
@@ -1296,6 +1384,7 @@ void *kernel_for(int method, int f32) {
   if (method == M_MRNE) return f32 ? (void *)k_krylov<M_MRNE, float, GRP> : (void *)k_krylov<M_MRNE, double, GRP>;
   if (method == M_CGNE) return f32 ? (void *)k_krylov<M_CGNE, float, GRP> : (void *)k_krylov<M_CGNE, double, GRP>;
   if (method == M_ABG) return f32 ? (void *)k_krylov<M_ABG, float, GRP> : (void *)k_krylov<M_ABG, double, GRP>;
+  if (method == M_BAG) return f32 ? (void *)k_krylov<M_BAG, float, GRP> : (void *)k_krylov<M_BAG, double, GRP>;
   return f32 ? (void *)k_krylov<M_SWEEP, float, GRP> : (void *)k_krylov<M_SWEEP, double, GRP>;
 }
 
@@ -1570,7 +1659,7 @@ lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
   // AB-GMRES: the cost of the grid path grows with the basis (reductions over
   // every SM's partials), which a probe of a few iterations does not see; the
   // grid is taken only when no cluster can hold the problem
-  const bool abg = base.method == M_ABG;
+  const bool abg = base.method == M_ABG || base.method == M_BAG;
   const int save_mode = ctx->cluster_mode, save_cs = ctx->cluster_size_override;
   const lpk_stats save_stats = ctx->stats;
   double best = 1e300;
@@ -1636,23 +1725,24 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
 
 }  // namespace
 
-lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
-                        const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
-                        KrylovResult *out, double *hist) {
-  if (method != LPK_MRNE && method != LPK_CGNE && method != LPK_ABGMRES) {
-    ctx->err = "unknown Krylov solver";
-    return LPK_INVALID_ARG;
-  }
+namespace {
+
+// one persistent launch of the Krylov kernel (kmethod: M_MRNE, M_CGNE, M_ABG
+// or M_BAG; rn is the n-space right-hand side of M_BAG)
+lpk_status krylov_run(lpk_ctx *ctx, DevProblem &P, int kmethod, int precision, int ell, double omega,
+                      const double *f_hat, const double *rn, double tol, int maxit, double *dw, double *dy_hat,
+                      KrylovResult *out, double *hist) {
   lpk_status st;
   if ((st = ensure_kctl(ctx)) != LPK_OK) return st;
   Workspace W;
   if ((st = get_ws(ctx, P, W)) != LPK_OK) return st;
   KArgs A = base_args(ctx, P, W, ell, omega);
   A.f = f_hat;
+  A.rn = rn;
   A.tol = tol;
   A.maxit = maxit;
-  A.method = method == LPK_MRNE ? M_MRNE : method == LPK_CGNE ? M_CGNE : M_ABG;
-  if (A.method == M_ABG && (st = get_gmres(ctx, P, maxit, A)) != LPK_OK) return st;
+  A.method = kmethod;
+  if ((kmethod == M_ABG || kmethod == M_BAG) && (st = get_gmres(ctx, P, maxit, A)) != LPK_OK) return st;
   // FP64: the paper's recurrences; up to 3 restarts when the explicit residual
   // does not confirm the recurrence.  Mixed: sweeps over the FP32 copy of the
   // scaled matrix with FP64 accumulation, w-space images by FP64 CSC products.
@@ -1676,6 +1766,25 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   out->iters32 = precision == LPK_MIXED ? h->iters : 0;
   out->escalations = 0;
   return LPK_OK;
+}
+
+}  // namespace
+
+lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
+                        const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
+                        KrylovResult *out, double *hist) {
+  if (method != LPK_MRNE && method != LPK_CGNE && method != LPK_ABGMRES) {
+    ctx->err = "unknown Krylov solver";
+    return LPK_INVALID_ARG;
+  }
+  const int km = method == LPK_MRNE ? M_MRNE : method == LPK_CGNE ? M_CGNE : M_ABG;
+  return krylov_run(ctx, P, km, precision, ell, omega, f_hat, nullptr, tol, maxit, dw, dy_hat, out, hist);
+}
+
+lpk_status krylov_solve_ls(lpk_ctx *ctx, DevProblem &P, int precision, int ell, double omega, const double *r_n,
+                           const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
+                           KrylovResult *out) {
+  return krylov_run(ctx, P, M_BAG, precision, ell, omega, f_hat, r_n, tol, maxit, dw, dy_hat, out, nullptr);
 }
 
 lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int ell, double omega,

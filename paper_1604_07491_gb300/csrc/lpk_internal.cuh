@@ -211,6 +211,11 @@ lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int 
                       const double *g_hat, double *z, double *u);
 // persistent Krylov solve on caller-supplied device memory (no allocation)
 size_t krylov_scratch_doubles(const DevProblem &P);
+// BA-GMRES with NR-SOR on min ||A_hat^T dy_hat - r|| (r_n: n-space, kept
+// columns; f_hat = A_hat r: m-space, for the explicit residual); dw = A_hat^T dy_hat
+lpk_status krylov_solve_ls(lpk_ctx *ctx, DevProblem &P, int precision, int ell, double omega, const double *r_n,
+                           const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
+                           KrylovResult *out);
 lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int precision, int ell, double omega,
                                 const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
                                 KrylovResult *out, double *ws);

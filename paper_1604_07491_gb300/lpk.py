@@ -29,7 +29,7 @@ NE_SSOR, NE_SOR = 0, 1
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
            "lpk_reset_stats", "lpk_set_exec", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
-           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_lp_solve",
+           "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_ls_solve", "lpk_lp_solve",
            "lpk_lp_solve_batch", "lpk_server_default_config", "lpk_server_create", "lpk_server_destroy",
            "lpk_server_now", "lpk_server_submit", "lpk_server_wait", "lpk_server_stats"]
 
@@ -51,7 +51,8 @@ class Options(C.Structure):
                 ("sigma_max", C.c_double), ("eps_in0", C.c_double), ("omega", C.c_double),
                 ("start_tol", C.c_double), ("backtrack", C.c_double), ("max_ipm", C.c_int32),
                 ("max_krylov", C.c_int32), ("inner_sweeps", C.c_int32), ("solver", C.c_int32),
-                ("precision", C.c_int32), ("verbose", C.c_int32), ("color_seed", C.c_uint64)]
+                ("precision", C.c_int32), ("verbose", C.c_int32), ("color_seed", C.c_uint64),
+                ("corrector", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -141,6 +142,7 @@ def load():
         "lpk_sweep": (I32, [P, P, P, P, I32, I32, D, I32, P, P, I32]),
         "lpk_ne_solve": (I32, [P, P, P, P, I32, D, I32, I32, D, I32, P, P, C.POINTER(KrylovInfo), I32]),
         "lpk_lp_solve": (I32, [P, P, P, P, C.POINTER(Options), P, P, P, C.POINTER(Info), I32]),
+        "lpk_ls_solve": (I32, [P, P, P, P, I32, D, I32, D, I32, P, P, C.POINTER(KrylovInfo), I32]),
         "lpk_ne_solve_noalloc": (I32, [P, P, P, P, I32, D, I32, I32, D, I32, P, P,
                                        C.POINTER(KrylovInfo)]),
         "lpk_lp_solve_batch": (I32, [I32, C.POINTER(P), C.POINTER(P), C.POINTER(P), C.POINTER(Options),
@@ -356,6 +358,18 @@ class Problem:
         _check(self.ctx.handle, load().lpk_ne_solve(self.ctx.handle, self._h, p, _ptr(f)[0],
                                                     inner_sweeps, omega, solver, precision, tol,
                                                     max_iter, _ptr(dy)[0], _ptr(dw)[0],
+                                                    C.byref(ki), dev))
+        return dy, dw, ki.as_dict()
+
+    def ls_solve(self, d2, r, inner_sweeps=2, omega=1.0, precision=FP64, tol=1e-10, max_iter=0):
+        """Corrector least squares min ||diag(sqrt d2) A^T dy - r|| by BA-GMRES
+        (NR-SOR): returns (dy[m], dw[n], krylov info dict)."""
+        d2, r = _f64(d2), _f64(r)
+        dy, dw = _like(r, self.m), _like(r, self.n)
+        ki = KrylovInfo()
+        p, dev = _ptr(d2)
+        _check(self.ctx.handle, load().lpk_ls_solve(self.ctx.handle, self._h, p, _ptr(r)[0], inner_sweeps, omega,
+                                                    precision, tol, max_iter, _ptr(dy)[0], _ptr(dw)[0],
                                                     C.byref(ki), dev))
         return dy, dw, ki.as_dict()
 

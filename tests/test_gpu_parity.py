@@ -276,6 +276,53 @@ def test_lp_solve_abgmres(lpk, pctx, orc, name, precision):
         assert rel(x, ox) < 1e-6
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "medium_0.05", "assignment"])
+def test_ls_solve_bagmres_parity(lpk, pctx, orc, name, precision):
+    """The corrector stage in least-squares form (Sec. 3.2) by BA-GMRES with
+    NR-SOR: min ||diag(sqrt d2) A^T dy - r||.  dw is the projection of r onto
+    the row space of A D, unique; the GPU (classical Gram-Schmidt with
+    reorthogonalisation) and the oracle (modified Gram-Schmidt) agree on it and
+    on the iteration count."""
+    lp = LPS[name]()
+    P = lpk.Problem.from_lp(pctx, lp)
+    color, perm, cptr = P.coloring()
+    rng = np.random.default_rng(21)
+    d2 = np.exp(rng.uniform(-3, 3, lp.n))
+    r = rng.standard_normal(lp.n)
+    ell, tol = 2, 1e-9
+    ody, odw, oinfo = orc.ls_solve(lp.m, lp.n, lp.row_ptr, lp.col_idx, lp.val, perm, d2, r, ell, 1.0, tol,
+                                   10 * lp.m)
+    dy, dw, info = P.ls_solve(d2, r, inner_sweeps=ell, precision=precision, tol=tol, max_iter=10 * lp.m)
+    assert oinfo["converged"] and info["converged"], (oinfo, info)
+    assert not info["breakdown"]
+    A = lp.scipy()
+    assert rel(dw, np.sqrt(d2) * (A.T @ dy)) < 1e-9
+    f = A @ (np.sqrt(d2) * r)
+    assert np.linalg.norm(f - A @ (np.sqrt(d2) * dw)) <= 1e-5 * np.linalg.norm(f)
+    assert rel(dw, odw) < 1e-5
+    if precision == 0:
+        assert abs(info["iters"] - oinfo["iters"]) <= max(1, oinfo["iters"] // 50)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["tiny", "assignment"])
+def test_lp_solve_bagmres_corrector(lpk, pctx, orc, name, precision):
+    lp, kw = _lp_case(name)
+    kw = dict(kw, solver=2, inner_sweeps=max(2, kw["inner_sweeps"]))
+    P = lpk.Problem.from_lp(pctx, lp)
+    x, y, s, info = P.lp_solve(lp.b, lp.c, precision=precision, corrector=1, **kw)
+    assert info["status_name"] == "OK", info
+    okw = dict(kw)
+    okw["method"] = okw.pop("solver")
+    ox, oy, os_, oinfo = _oracle_lp(orc, name + "_ba", lp, dict(okw, corrector_ba=1))
+    assert oinfo["status_name"] == "OK"
+    ref = oinfo["obj_primal"]
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
+    pinf, dinf, gap = certs(lp, x, y, s)
+    assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+
+
 def test_lp_solve_device_tensors_and_determinism(lpk, ctx):
     lp = gen.tiny_lp()
     P = lpk.Problem.from_lp(ctx, lp, device="cuda")
