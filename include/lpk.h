@@ -290,7 +290,10 @@ LPK_API lpk_status lpk_ne_solve_noalloc(lpk_ctx *ctx, lpk_problem *P, const doub
  * A diag(sqrt(d2)) dw = A diag(sqrt(d2)) r, may be NULL).  Convergence: the
  * explicit scaled residual ||f_hat - A_hat dw|| <= tol ||f_hat|| with
  * f_hat = A_hat r (kinfo->converged).  inner_sweeps = NR-SOR sweeps per
- * application, max_iter 0 -> m.  Layout and staging as lpk_ne_solve. */
+ * application, max_iter 0 -> m.  Layout and staging as lpk_ne_solve.
+ * precision is accepted for symmetry and ignored: BA-GMRES sweeps in FP64
+ * (a left preconditioner must have the null space of the scaled matrix; the
+ * FP32 copy's differs and the residual stalls near 1e-7). */
 LPK_API lpk_status lpk_ls_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *r,
                                 int32_t inner_sweeps, double omega, int32_t precision, double tol,
                                 int32_t max_iter, double *dy, double *dw, lpk_krylov_info *kinfo,

@@ -1781,10 +1781,15 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
   return krylov_run(ctx, P, km, precision, ell, omega, f_hat, nullptr, tol, maxit, dw, dy_hat, out, hist);
 }
 
+// BA-GMRES sweeps in FP64 at either precision: left preconditioning finds the
+// least-squares solution only if the preconditioner has the null space of
+// A_hat, and NR-SOR over the FP32 copy of A_hat has that of the rounded
+// matrix (measured: the explicit residual stalls near 1e-7).
 lpk_status krylov_solve_ls(lpk_ctx *ctx, DevProblem &P, int precision, int ell, double omega, const double *r_n,
                            const double *f_hat, double tol, int maxit, double *dw, double *dy_hat,
                            KrylovResult *out) {
-  return krylov_run(ctx, P, M_BAG, precision, ell, omega, f_hat, r_n, tol, maxit, dw, dy_hat, out, nullptr);
+  (void)precision;
+  return krylov_run(ctx, P, M_BAG, LPK_FP64, ell, omega, f_hat, r_n, tol, maxit, dw, dy_hat, out, nullptr);
 }
 
 lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int ell, double omega,
