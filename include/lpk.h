@@ -104,7 +104,11 @@ typedef struct lpk_options {
   uint64_t color_seed;
   int32_t corrector;  /* 0: corrector stage by `solver`; 1: by BA-GMRES with
                          NR-SOR on its least-squares form (Sec. 3.2)       */
-  int32_t reserved;
+  int32_t max_correctors; /* 0..10 multiple centrality correctors per
+                         iteration after the predictor-corrector direction
+                         (the multi-corrector framework Sec. 4.3 and 5 name;
+                         Gondzio's method), each one more Krylov solve;
+                         0 = the paper's single corrector (default)        */
 } lpk_options;
 
 /* Result summary of lpk_lp_solve.  gamma is the error measure of
@@ -119,6 +123,8 @@ typedef struct lpk_info {
   int32_t krylov_failures;
   double gamma, rel_gap, pinf, dinf, mu, obj_primal, obj_dual;
   double solve_ms;
+  int32_t correctors;  /* centrality correctors accepted over the solve */
+  int32_t reserved;
 } lpk_info;
 
 /* Result of one Krylov solve: iterations over all restarts, whether the

@@ -18,6 +18,9 @@
  *   Algorithm 1     Mehrotra predictor-corrector,      -> orc_lp_solve
  *                   Eq. (steplength), sigma rule, Gamma (Eq. errorMeasureDef),
  *                   centrality backtracking, eps_in schedule of Sec. 4.2
+ *   Sec. 4.3 / 5    multiple centrality correctors    -> ipm_core (max_correctors)
+ *                   (the multi-corrector framework the paper names as the
+ *                   way to fewer interior-point iterations; Gondzio 1996)
  * The multicolor row order (rows of one color share no column) is not in the
  * paper, which sweeps rows in natural order; the oracle applies the same
  * order as the GPU so that sweeps can be compared element by element.
@@ -648,6 +651,7 @@ void orc_default_options(orc_options *o) {
   o->method = ORC_MRNE;
   o->color_seed = 0x5EEDULL;
   o->corrector_ba = 0;
+  o->max_correctors = 0;
 }
 
 static double step_len(int32_t n, const double *x, const double *dx, double eta) {
@@ -793,9 +797,53 @@ static int32_t ipm_core(int32_t m, int32_t n, const int64_t *rp, const int32_t *
       }
       for (int32_t i = 0; i < m; ++i) dy[i] = dya[i] + dyc[i];
     }
-    /* trial steps and centrality backtracking */
+    /* trial steps of the combined direction */
     ap = step_len(n, x, dx, opt->eta);
     ad = step_len(n, s, ds, opt->eta);
+    /* multiple centrality correctors (Gondzio): aim at step lengths larger by
+       GZ_DELTA, move the complementarity products of that trial point that
+       fall outside [GZ_BMIN, GZ_BMAX] * sigma mu back to the box, solve the
+       Newton system for that change of the third block (r_p = r_d = 0) and
+       keep the corrected direction while it lengthens the shorter step by at
+       least GZ_GAMMA * GZ_DELTA.  reading: the parameter values are the ones
+       of the published method; sigma mu is this iteration's centring target;
+       a corrector whose Krylov solve does not converge is not used. */
+    if (opt->max_correctors > 0 && sigma > 0.0) {
+      const double GZ_DELTA = 0.1, GZ_BMIN = 0.1, GZ_BMAX = 10.0, GZ_GAMMA = 0.1;
+      double *hg = dalloc(n), *dwg = dalloc(n), *dyg = dalloc(m), *dx2 = dalloc(n), *ds2 = dalloc(n);
+      for (int32_t kc = 0; kc < opt->max_correctors; ++kc) {
+        double amin = fmin(ap, ad);
+        if (amin >= 1.0) break;
+        double apt = fmin(1.0, ap + GZ_DELTA), adt = fmin(1.0, ad + GZ_DELTA);
+        double lo = GZ_BMIN * sigma * mu, hi = GZ_BMAX * sigma * mu;
+        for (int32_t j = 0; j < n; ++j) {
+          double v = (x[j] + apt * dx[j]) * (s[j] + adt * ds[j]), t = 0.0;
+          if (v < lo) t = lo - v;
+          else if (v > hi) t = fmax(hi - v, -hi);
+          hg[j] = -t / s[j];                       /* the third block S dx + X ds = t */
+        }
+        spmv(m, rp, ci, val, hg, f);
+        orc_ne_solve(m, n, rp, ci, val, perm, d2, f, ell, om, meth, eps_in, maxit, dyg, dwg, &ki);
+        info->krylov_iters_total += ki.iters;
+        if (!ki.converged) break;
+        for (int32_t j = 0; j < n; ++j) {
+          double dsc = -dwg[j] / d[j];
+          double dxc = -d2[j] * dsc - hg[j];
+          dx2[j] = dx[j] + dxc;
+          ds2[j] = ds[j] + dsc;
+        }
+        double ap2 = step_len(n, x, dx2, opt->eta), ad2 = step_len(n, s, ds2, opt->eta);
+        if (!(fmin(ap2, ad2) >= amin + GZ_GAMMA * GZ_DELTA)) break;
+        memcpy(dx, dx2, sizeof(double) * (size_t)n);
+        memcpy(ds, ds2, sizeof(double) * (size_t)n);
+        for (int32_t i = 0; i < m; ++i) dy[i] += dyg[i];
+        ap = ap2;
+        ad = ad2;
+        info->correctors++;
+      }
+      free(hg); free(dwg); free(dyg); free(dx2); free(ds2);
+    }
+    /* centrality backtracking */
     double tau = 1.0;
     for (int32_t tr = 0; tr < 60; ++tr) {
       double a1 = tau * ap, a2 = tau * ad, mn = INFINITY, sm = 0.0;

@@ -51,6 +51,9 @@ typedef struct {
   uint64_t color_seed;
   int32_t verbose;     /* 1: one line per interior-point iteration on stderr */
   int32_t corrector_ba;/* 1: corrector stage by BA-GMRES (NR-SOR), Sec. 3.2   */
+  int32_t max_correctors; /* multiple centrality correctors per iteration (0: the
+                             paper's single corrector)                       */
+  int32_t pad;
 } orc_options;
 
 typedef struct {
@@ -60,6 +63,8 @@ typedef struct {
   int32_t n_colors;
   int32_t krylov_failures;
   double gamma, rel_gap, pinf, dinf, mu, obj_primal, obj_dual;
+  int32_t correctors;  /* centrality correctors accepted over the solve      */
+  int32_t pad;
 } orc_info;
 
 typedef struct {

@@ -459,7 +459,7 @@ LPK_API lpk_status lpk_lp_solve(lpk_ctx *ctx, lpk_problem *P, const double *b, c
   if (!b || !c || !x || !y || !s || o.inner_sweeps < 1 || !(o.omega > 0.0 && o.omega < 2.0) ||
       !(o.eta > 0.0 && o.eta < 1.0) || o.max_ipm < 0 || o.max_krylov < 0 ||
       (o.solver != LPK_MRNE && o.solver != LPK_CGNE && o.solver != LPK_ABGMRES) ||
-      (o.corrector != 0 && o.corrector != 1) ||
+      (o.corrector != 0 && o.corrector != 1) || o.max_correctors < 0 || o.max_correctors > 10 ||
       (o.precision != LPK_FP64 && o.precision != LPK_MIXED)) {
     ctx->err = "lpk_lp_solve: invalid arguments";
     return LPK_INVALID_ARG;

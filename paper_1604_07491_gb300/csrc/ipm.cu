@@ -98,6 +98,20 @@ __global__ void k_muaf(int n, const double *x, const double *s, const double *dx
   grid_reduce<1, 1>(v, mn, R);
 }
 
+// centrality corrector: v = (x + apt dx)(s + adt ds) moved back to [lo, hi]
+// (t = target - v, at least -hi), as the third block S dx + X ds = t: h = -t / s
+__global__ void k_gz_rhs(int n, const double *x, const double *s, const double *dx, const double *ds, double apt,
+                         double adt, double lo, double hi, double *h) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) {
+    const double v = (x[j] + apt * dx[j]) * (s[j] + adt * ds[j]);
+    double t = 0.0;
+    if (v < lo) t = lo - v;
+    else if (v > hi) t = fmax(hi - v, -hi);
+    h[j] = -t / s[j];
+  }
+}
+
 // h = S^-1 (dX_af ds_af - sigma mu e)
 __global__ void k_h(int n, const double *dxa, const double *dsa, const double *s, double smu, double *h) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -270,9 +284,9 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
   info = lpk_info{};
   info.n_colors = P.n_colors;
 
-  // workspace (kept with the problem): 10 m-vectors, 17 n-vectors, flags
+  // workspace (kept with the problem): 12 m-vectors, 21 n-vectors, flags
   const size_t mm = m > 0 ? m : 1, nn = n > 0 ? n : 1;
-  const size_t need = sizeof(double) * (10 * mm + 17 * nn + 4);
+  const size_t need = sizeof(double) * (12 * mm + 21 * nn + 4);
   if (P.ipm_bytes < need) {
     dev_free(st, P.ipm_buf);
     P.ipm_buf = nullptr;
@@ -284,7 +298,7 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
 
   // checks on b and c (input numbering)
   {
-    int *flags = (int *)(buf + 10 * mm + 17 * nn);
+    int *flags = (int *)(buf + 12 * mm + 21 * nn);
     LPK_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int), st));
     int len = std::max(P.m_in, P.n_in);
     if (len > 0)
@@ -313,10 +327,11 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
   auto take_m = [&]() { double *r = q; q += mm; return r; };
   auto take_n = [&]() { double *r = q; q += nn; return r; };
   double *b = take_m(), *y = take_m(), *rp = take_m(), *f = take_m(), *dya = take_m(), *dyc = take_m(),
-         *dy = take_m(), *tm = take_m(), *tm2 = take_m(), *tm3 = take_m();
+         *dy = take_m(), *tm = take_m(), *tm2 = take_m(), *tm3 = take_m(), *dyg = take_m(), *dy2 = take_m();
   double *c = take_n(), *x = take_n(), *s = take_n(), *rd = take_n(), *d2 = take_n(), *d = take_n(),
          *hv = take_n(), *dwa = take_n(), *dxa = take_n(), *dsa = take_n(), *dwc = take_n(), *dx = take_n(),
-         *ds = take_n(), *hh = take_n(), *tn = take_n(), *tn2 = take_n(), *tn3 = take_n();
+         *ds = take_n(), *hh = take_n(), *tn = take_n(), *tn2 = take_n(), *tn3 = take_n(), *hg = take_n(),
+         *dwg = take_n(), *dx2 = take_n(), *ds2 = take_n();
   (void)tm3; (void)tn3; (void)tn2;
   gather_m(ctx, P, b_in, b);
   gather_n(ctx, P, c_in, c);
@@ -427,6 +442,45 @@ lpk_status lp_solve_dev(lpk_ctx *ctx, DevProblem &P, const double *b_in, const d
     // trial steps of the combined direction, then centrality backtracking
     double ap0 = std::min(1.0, o.eta * h[1]), ad0 = std::min(1.0, o.eta * h[2]);
     if (DX == dxa) { ap0 = ap; ad0 = ad; }
+    // multiple centrality correctors (Gondzio): aim at step lengths larger by
+    // GZ_DELTA, move the complementarity products of that trial point that fall
+    // outside [GZ_BMIN, GZ_BMAX] sigma mu back to the box, solve the Newton
+    // system for that change of its third block (r_p = r_d = 0) and keep the
+    // corrected direction while it lengthens the shorter step by at least
+    // GZ_GAMMA GZ_DELTA; a corrector whose Krylov solve fails is not used
+    if (o.max_correctors > 0 && DX != dxa && sigma > 0.0) {
+      constexpr double GZ_DELTA = 0.1, GZ_BMIN = 0.1, GZ_BMAX = 10.0, GZ_GAMMA = 0.1;
+      double *DX2 = DX == dx ? dx2 : dx, *DS2 = DS == ds ? ds2 : ds, *DY2 = DY == dy ? dy2 : dy;
+      for (int kc = 0; kc < o.max_correctors; ++kc) {
+        const double amin = std::min(ap0, ad0);
+        if (amin >= 1.0) break;
+        const double apt = std::min(1.0, ap0 + GZ_DELTA), adt = std::min(1.0, ad0 + GZ_DELTA);
+        if (n > 0)
+          LPK_LAUNCH(ctx, k_gz_rhs, eb(n), TPB, 0, st, n, x, s, DX, DS, apt, adt, GZ_BMIN * sigma * mu,
+                     GZ_BMAX * sigma * mu, hg);
+        spmv_csr(ctx, P, hg, f, nullptr, 1.0);
+        if (o.corrector == 1) {
+          if (n > 0) LPK_LAUNCH(ctx, k_div, eb(n), TPB, 0, st, n, hg, d, tn3);
+          if ((rc = ls_solve_scaled(ctx, P, tn3, f, ell, om, prec, eps_in, maxit, dyg, dwg, tm2, &kr)) != LPK_OK)
+            return rc;
+        } else if ((rc = ne_solve_scaled(ctx, P, f, ell, om, solver, prec, eps_in, maxit, dyg, dwg, tm2, &kr)) !=
+                   LPK_OK) {
+          return rc;
+        }
+        info.krylov_iters_total += kr.iters;
+        if (!kr.converged) break;
+        LPK_LAUNCH(ctx, k_dir_corr, RG, TPB, 0, st, m, n, DX, DS, dwg, d, d2, hg, x, s, DX2, DS2, DY, dyg, DY2, R);
+        if ((rc = red_fetch(ctx, 3)) != LPK_OK) return rc;
+        const double ap1 = std::min(1.0, o.eta * h[1]), ad1 = std::min(1.0, o.eta * h[2]);
+        if (!(std::min(ap1, ad1) >= amin + GZ_GAMMA * GZ_DELTA)) break;
+        std::swap(DX, DX2);
+        std::swap(DS, DS2);
+        std::swap(DY, DY2);
+        ap0 = ap1;
+        ad0 = ad1;
+        info.correctors++;
+      }
+    }
     double tau = 1.0;
     bool accepted = false;
     for (int base = 0; base < 60 && !accepted; base += NTRIAL) {

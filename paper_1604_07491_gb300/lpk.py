@@ -52,7 +52,7 @@ class Options(C.Structure):
                 ("start_tol", C.c_double), ("backtrack", C.c_double), ("max_ipm", C.c_int32),
                 ("max_krylov", C.c_int32), ("inner_sweeps", C.c_int32), ("solver", C.c_int32),
                 ("precision", C.c_int32), ("verbose", C.c_int32), ("color_seed", C.c_uint64),
-                ("corrector", C.c_int32), ("reserved", C.c_int32)]
+                ("corrector", C.c_int32), ("max_correctors", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -60,7 +60,7 @@ class Info(C.Structure):
                 ("n_colors", C.c_int32), ("krylov_failures", C.c_int32), ("gamma", C.c_double),
                 ("rel_gap", C.c_double), ("pinf", C.c_double), ("dinf", C.c_double),
                 ("mu", C.c_double), ("obj_primal", C.c_double), ("obj_dual", C.c_double),
-                ("solve_ms", C.c_double)]
+                ("solve_ms", C.c_double), ("correctors", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

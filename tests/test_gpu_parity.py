@@ -323,6 +323,29 @@ def test_lp_solve_bagmres_corrector(lpk, pctx, orc, name, precision):
     assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["tiny", "assignment"])
+def test_lp_solve_multiple_centrality_correctors(lpk, pctx, orc, name):
+    """Gondzio's multiple centrality correctors (max_correctors = 2) on top of
+    the predictor-corrector direction: the oracle's optimum and certificates,
+    correctors accepted, no more interior-point iterations than without."""
+    lp, kw = _lp_case(name)
+    if name == "assignment":
+        kw = dict(kw, solver=2)
+    P = lpk.Problem.from_lp(pctx, lp)
+    x, y, s, info = P.lp_solve(lp.b, lp.c, max_correctors=2, **kw)
+    assert info["status_name"] == "OK", info
+    okw = dict(kw)
+    if "solver" in okw:
+        okw["method"] = okw.pop("solver")
+    ox, oy, os_, oinfo = _oracle_lp(orc, name + "_gz", lp, dict(okw, max_correctors=2))
+    assert oinfo["status_name"] == "OK"
+    assert abs(info["obj_primal"] - oinfo["obj_primal"]) <= 1e-7 * abs(oinfo["obj_primal"])
+    pinf, dinf, gap = certs(lp, x, y, s)
+    assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+    assert info["correctors"] > 0
+    assert abs(info["ipm_iters"] - oinfo["ipm_iters"]) <= 2
+
+
 def test_lp_solve_device_tensors_and_determinism(lpk, ctx):
     lp = gen.tiny_lp()
     P = lpk.Problem.from_lp(ctx, lp, device="cuda")

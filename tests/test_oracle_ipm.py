@@ -155,3 +155,23 @@ def test_tiny_lp_with_bagmres_corrector_matches_highs(orc, method):
     ref = highs(lp)
     assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
     assert certificates_ok(lp, x, y, s)
+
+
+@pytest.mark.parametrize("name", ["tiny", "micro_rank_deficient", "assignment"])
+def test_multiple_centrality_correctors_reach_the_optimum(orc, name):
+    # the multi-corrector interior-point framework (Sec. 4.3 and 5): the same
+    # optimum, at most as many interior-point iterations, correctors accepted
+    if name == "tiny":
+        lp, kw = gen.tiny_lp(), dict(inner_sweeps=1)
+    elif name == "assignment":
+        lp, kw = gen.assignment_lp(), dict(inner_sweeps=3, method=2)
+    else:
+        lp, kw = gen.medium_lp(scale=0.004, seed=21), dict(inner_sweeps=3)
+    x0, y0, s0, i0 = orc.lp_solve_lp(lp, **kw)
+    x, y, s, info = orc.lp_solve_lp(lp, max_correctors=2, **kw)
+    assert info["status_name"] == "OK" and i0["status_name"] == "OK"
+    ref = highs(lp)
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * max(1.0, abs(ref))
+    assert certificates_ok(lp, x, y, s)
+    assert info["correctors"] > 0
+    assert info["ipm_iters"] <= i0["ipm_iters"]
