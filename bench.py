@@ -304,6 +304,8 @@ def main():
     ap.add_argument("--workload", default="assignment", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="LPs per step solved side by side (0: workload's)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cluster", type=int, default=0, choices=[0, 4, 8, 16],
+                    help="batch path: CTAs per LP's cluster (0: chosen from the problem)")
     ap.add_argument("--solver", default="", choices=[""] + sorted(SOLVERS),
                     help="Krylov solver (default: the workload's)")
     ap.add_argument("--compare-fp64", type=int, default=3,
@@ -363,6 +365,9 @@ def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
     main_stream = torch.cuda.current_stream(dev)
     streams = [main_stream] if B == 1 else [torch.cuda.Stream(dev) for _ in range(B)]
     ctxs = [lpk.Context(local, st.cuda_stream) for st in streams]
+    if B > 1 and args.cluster:
+        for c in ctxs:
+            c.set_exec(lpk.EXEC_BATCH, args.cluster)
     probs = [lpk.Problem.from_lp(ctxs[i], lps[i], device=dev) for i in range(B)]
     bs = [torch.from_numpy(lp.b).to(dev) for lp in lps]
     cs = [torch.from_numpy(lp.c).to(dev) for lp in lps]
