@@ -50,6 +50,9 @@ WORKLOADS = {
                        opts=dict(solver=2, inner_sweeps=5, omega=1.0, max_krylov=6000), batch=8),
     "serving": dict(desc="Poisson stream (rate 50/s) of LPs, m log-uniform in [100, 20000], n=3m, 6 nnz/col",
                     opts=dict(solver=2, inner_sweeps=3, omega=1.0), batch=1),
+    "large_x8": dict(desc="large LP matrix (m=150000, n=434580, power-law column degrees) replicated 8x "
+                          "block-diagonally: SpMV bandwidth, not L2-resident",
+                     opts=dict(solver=0, inner_sweeps=1), batch=1),
 }
 
 
@@ -348,6 +351,8 @@ def main():
 
     if args.workload == "serving":
         line = run_serving(args, wl, opts, lpk, local, rank, world, barrier)
+    elif args.workload == "large_x8":
+        line = run_bandwidth(args, wl, lpk, torch, dev, local, rank, world, barrier)
     else:
         line = run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist)
     if rank == 0 and line is not None:
@@ -488,6 +493,79 @@ def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
         "roofline": roofline(stats, lp0, args.precision, total_ms,
                              MEASURED_TRAFFIC.get((args.workload, args.precision, opts["solver"]))),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": stats["launches"], "clocks": clk.summary(),
+    }
+
+
+def replicated_csr(lp, copies):
+    """lp's matrix repeated `copies` times on the block diagonal (CSR)."""
+    import numpy as np
+    nnz = int(lp.row_ptr[-1])
+    rp = np.concatenate([lp.row_ptr[:-1] + k * nnz for k in range(copies)] + [[copies * nnz]]).astype(np.int64)
+    ci = np.concatenate([lp.col_idx + k * lp.n for k in range(copies)]).astype(np.int32)
+    val = np.tile(lp.val, copies)
+    return copies * lp.m, copies * lp.n, rp, ci, val
+
+
+def run_bandwidth(args, wl, lpk, torch, dev, local, rank, world, barrier):
+    """Bandwidth of the sparse products on a matrix larger than L2: y = A x
+    and w = A^T y in FP64 through lpk_spmv (gather to the internal numbering,
+    CSR or CSC product, scatter back).  The sweep is not measured here: on the
+    grid path each warp keeps a slot per row it sweeps in shared memory, which
+    caps a sweep at about 1,400 slots per warp (rows / 1,216 warps + colors),
+    below this matrix's 1.2 M rows with 400+ colors."""
+    from paper_1604_07491_gb300 import gen
+    base = gen.large_lp(1.0)
+    m, n, rp, ci, val = replicated_csr(base, 8)
+    nnz = int(rp[-1])
+    ctx = lpk.Context(local, torch.cuda.current_stream(dev).cuda_stream)
+    P = lpk.Problem(ctx, m, n, torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev),
+                    torch.from_numpy(val).to(dev))
+    gx = torch.Generator(device="cpu").manual_seed(7)
+    x = torch.rand(n, generator=gx, dtype=torch.float64).to(dev)
+    yv = torch.rand(m, generator=gx, dtype=torch.float64).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(max(1, args.warmup)):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            barrier()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    with ClockSampler(local) as clk:
+        ms_a = timed(lambda: P.spmv(x), args.steps)
+        ms_t = timed(lambda: P.spmv(yv, transpose=True), args.steps)
+    hbm, src = peaks()
+    # algorithmic bytes: value + index + gathered vector entry per nonzero
+    # (8 + 4 + 8), pointer + result per row/column (4 + 8), and the gather and
+    # scatter between input and internal numbering (16 B per entry of x and y)
+    b_a = nnz * 20 + m * 12 + 16 * (n + m)
+    b_t = nnz * 20 + n * 12 + 16 * (n + m)
+    if rank != 0:
+        return None
+    ga, gt = b_a / (ms_a / 1e3) / 1e9, b_t / (ms_t / 1e3) / 1e9
+    return {
+        "metric": "SpMV HBM GB/s (A x and A^T y, FP64)", "value": ga, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_a, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"large_x8: {wl['desc']}", "m": m, "n": n, "nnz": nnz,
+                   "n_colors": P.n_colors, "l2": "256 MB buffer written between timed calls",
+                   "inputs": "resident in HBM"},
+        "spmv_csr": {"ms": ms_a, "bytes": b_a, "gbs": ga, "frac": ga / hbm},
+        "spmv_csc": {"ms": ms_t, "bytes": b_t, "gbs": gt, "frac": gt / hbm},
+        "roofline": {"bound": "hbm", "achieved": ga, "peak": hbm, "unit": "GB/s", "frac": ga / hbm,
+                     "traffic": None, "kernel": "lpk_spmv (k_gather, k_spmv_csr, k_scatter)",
+                     "peak_source": f"{src} hbm_gbs"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
     }
 
 
