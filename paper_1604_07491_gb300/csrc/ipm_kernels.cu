@@ -48,31 +48,51 @@ __global__ void k_scale_csc(int n, const int *__restrict__ cp, const int *__rest
   }
 }
 
-// y = sign * A x + add  (warp per row)
+// Sparse products with LPR lanes per row (or column): short rows leave most
+// of a warp idle with one row per warp, so a warp takes 32 / LPR rows at once
+// (more independent loads in flight per warp); the partial sums of a row are
+// combined by shuffles inside its LPR-lane group, in a fixed order.
+template <int LPR>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+  for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, LPR);
+  return v;
+}
+
+// y = sign * A x + add
+template <int LPR>
 __global__ void k_spmv_csr(int m, const int *__restrict__ rp, const int *__restrict__ ci,
                            const double *__restrict__ a, const double *__restrict__ x,
                            double *__restrict__ y, const double *__restrict__ add, double sign) {
-  const int lane = threadIdx.x & 31;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= m) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (int)(t / LPR), sub = (int)(t % LPR);
   double s = 0.0;
-  for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) s += a[k] * x[ci[k]];
-  s = warp_sum(s);
-  if (lane == 0) y[r] = sign * s + (add ? add[r] : 0.0);
+  if (r < m)
+    for (int k = __ldg(rp + r) + sub, k1 = __ldg(rp + r + 1); k < k1; k += LPR) s += __ldg(a + k) * __ldg(x + __ldg(ci + k));
+  s = group_sum<LPR>(s);  // every lane of the warp takes part
+  if (r < m && sub == 0) y[r] = sign * s + (add ? add[r] : 0.0);
 }
 
-// y = A^T x through the CSC (warp per column)
+// y = A^T x through the CSC
+template <int LPR>
 __global__ void k_spmv_csc(int n, const int *__restrict__ cp, const int *__restrict__ ri,
                            const double *__restrict__ at, const double *__restrict__ x,
                            double *__restrict__ y) {
-  const int lane = threadIdx.x & 31;
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (j >= n) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)(t / LPR), sub = (int)(t % LPR);
   double s = 0.0;
-  for (int q = cp[j] + lane; q < cp[j + 1]; q += 32) s += at[q] * x[ri[q]];
-  s = warp_sum(s);
-  if (lane == 0) y[j] = s;
+  if (j < n)
+    for (int q = __ldg(cp + j) + sub, q1 = __ldg(cp + j + 1); q < q1; q += LPR) s += __ldg(at + q) * __ldg(x + __ldg(ri + q));
+  s = group_sum<LPR>(s);
+  if (j < n && sub == 0) y[j] = s;
 }
+
+// lanes per row from the mean row length
+inline int lanes_for(long long nnz, long long rows) {
+  const long long avg = rows > 0 ? (nnz + rows - 1) / rows : 0;
+  return avg <= 8 ? 4 : avg <= 24 ? 8 : avg <= 64 ? 16 : 32;
+}
+inline int gblk(long long rows, int lpr, int tpb = TPB) { return (int)((rows * lpr + tpb - 1) / tpb); }
 
 __global__ void k_gather(int len, const int *__restrict__ idx, const double *__restrict__ in,
                          double *__restrict__ out) {
@@ -102,10 +122,24 @@ void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2) {
   if (P.n > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.n), TPB, 0, ctx->stream, P.n, P.cp, P.ri, P.at, d2, P.rho, P.aht);
 }
 void spmv_csr(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y, const double *add, double sign) {
-  if (P.m > 0) LPK_LAUNCH(ctx, k_spmv_csr, wblk(P.m), TPB, 0, ctx->stream, P.m, P.rp, P.ci, P.a, x, y, add, sign);
+  if (P.m <= 0) return;
+  cudaStream_t s = ctx->stream;
+  switch (lanes_for(P.nnz, P.m)) {
+    case 4: LPK_LAUNCH(ctx, k_spmv_csr<4>, gblk(P.m, 4), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
+    case 8: LPK_LAUNCH(ctx, k_spmv_csr<8>, gblk(P.m, 8), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
+    case 16: LPK_LAUNCH(ctx, k_spmv_csr<16>, gblk(P.m, 16), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
+    default: LPK_LAUNCH(ctx, k_spmv_csr<32>, gblk(P.m, 32), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
+  }
 }
 void spmv_csc(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y) {
-  if (P.n > 0) LPK_LAUNCH(ctx, k_spmv_csc, wblk(P.n), TPB, 0, ctx->stream, P.n, P.cp, P.ri, P.at, x, y);
+  if (P.n <= 0) return;
+  cudaStream_t s = ctx->stream;
+  switch (lanes_for(P.nnz, P.n)) {
+    case 4: LPK_LAUNCH(ctx, k_spmv_csc<4>, gblk(P.n, 4), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
+    case 8: LPK_LAUNCH(ctx, k_spmv_csc<8>, gblk(P.n, 8), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
+    case 16: LPK_LAUNCH(ctx, k_spmv_csc<16>, gblk(P.n, 16), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
+    default: LPK_LAUNCH(ctx, k_spmv_csc<32>, gblk(P.n, 32), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
+  }
 }
 void gather_m(lpk_ctx *ctx, const DevProblem &P, const double *in, double *out) {
   if (P.m > 0) LPK_LAUNCH(ctx, k_gather, tblk(P.m), TPB, 0, ctx->stream, P.m, P.in_row_of_pos, in, out);
