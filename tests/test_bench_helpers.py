@@ -1,0 +1,43 @@
+"""Host-side arithmetic of bench.py: algorithmic bytes, percentiles, the
+whole-job throughput and the block-diagonal replication used for the
+bandwidth workload.  CPU only."""
+import numpy as np
+import pytest
+
+import bench
+from paper_1604_07491_gb300 import gen
+
+
+def test_algorithmic_bytes_counts_each_unit():
+    m, n, nnz = 10, 30, 100
+    one = dict(sweep_passes=0, row_passes=0, csc_passes=0, krylov_iters=0, basis_passes=0)
+    assert bench.algorithmic_bytes(one, m, n, nnz, "mixed") == 0
+    assert bench.algorithmic_bytes(dict(one, sweep_passes=1), m, n, nnz, "mixed") == nnz * 24 + m * 28
+    assert bench.algorithmic_bytes(dict(one, sweep_passes=1), m, n, nnz, "fp64") == nnz * 28 + m * 28
+    assert bench.algorithmic_bytes(dict(one, row_passes=2), m, n, nnz, "fp64") == 2 * (nnz * 20 + m * 12)
+    assert bench.algorithmic_bytes(dict(one, csc_passes=1), m, n, nnz, "fp64") == nnz * 20 + n * 12
+    assert bench.algorithmic_bytes(dict(one, krylov_iters=1), m, n, nnz, "fp64") == 8 * (12 * n + 12 * m)
+    assert bench.algorithmic_bytes(dict(one, basis_passes=3), m, n, nnz, "fp64") == 3 * 8 * m
+
+
+def test_percentile_nearest_rank():
+    v = list(range(1, 101))
+    assert bench.percentile(v, 0.5) == 50 and bench.percentile(v, 0.99) == 99
+    assert bench.percentile([7.0], 0.99) == 7.0
+
+
+def test_weak_throughput_and_offsets():
+    assert bench.weak_throughput(2, 16, 5, 10000.0) == pytest.approx(16.0)
+    assert bench.replica_offsets(1, 4) == [4, 5, 6, 7]
+    assert bench.max_over_ranks(3.5, None) == 3.5
+
+
+def test_replicated_csr_is_block_diagonal():
+    lp = gen.tiny_lp()
+    m, n, rp, ci, val = bench.replicated_csr(lp, 3)
+    A = lp.scipy().toarray()
+    import scipy.sparse as sp
+    B = sp.csr_matrix((val, ci, rp), shape=(m, n)).toarray()
+    for k in range(3):
+        assert np.array_equal(B[k * lp.m:(k + 1) * lp.m, k * lp.n:(k + 1) * lp.n], A)
+    assert np.count_nonzero(B) == 3 * np.count_nonzero(A)
