@@ -107,12 +107,12 @@ struct Request {
 
 // Device memory one request holds while it runs: the prepared problem with
 // prepare's temporaries (at most 80 B per nonzero), the interior-point and
-// Krylov workspaces, and for AB-GMRES the basis sized to the iteration cap
-// (capped at 16 GiB, as the kernel caps it).
+// Krylov workspaces, and for AB-GMRES (or a BA-GMRES corrector) the basis
+// sized to the iteration cap (capped at 16 GiB, as the kernel caps it).
 int64_t request_bytes(const Request &r, int num_sms) {
   const int64_t m = r.m, n = r.n, nnz = (int64_t)r.ci.size();
   int64_t bytes = 80 * nnz + 8 * (24 * m + 32 * n) + (1 << 20);
-  if (r.opt.solver == LPK_ABGMRES) {
+  if (r.opt.solver == LPK_ABGMRES || r.opt.corrector == 1) {  // AB-GMRES or BA-GMRES basis
     const int64_t kmax = r.opt.max_krylov > 0 ? r.opt.max_krylov : m;
     const int64_t ld = (kmax + 4) & ~int64_t(3);
     const int64_t S = num_sms > 16 ? num_sms : 16;
