@@ -176,3 +176,28 @@ def test_server_memory_admission_and_errors(lpk):
         assert r[3]["status_name"] == "OK"
         pinf, dinf, gap = certs(lp, *r[:3])
         assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+
+
+def test_batch_assignment_in_the_bench_configuration(lpk, orc):
+    """The configuration bench.py times: assignment LPs (k = 14) side by side
+    on the batch path (8-CTA clusters), AB-GMRES with NE-SOR (ell = 3), mixed
+    precision; each LP against the oracle's objective and certificates."""
+    lps = [gen.assignment_lp(seed=gen.SEED_BASE + 3 + 1000 * i) for i in range(2)]
+    opts = dict(solver=2, inner_sweeps=3, precision=1)
+    streams = [torch.cuda.Stream() for _ in lps]
+    ctxs = [lpk.Context(0, st.cuda_stream) for st in streams]
+    try:
+        probs = [lpk.Problem.from_lp(c, lp) for c, lp in zip(ctxs, lps)]
+        res = lpk.solve_batch(probs, [lp.b for lp in lps], [lp.c for lp in lps], **opts)
+        sizes = {c.stats()["last_cluster_size"] for c in ctxs}
+    finally:
+        for c in ctxs:
+            c.close()
+    assert sizes == {8}
+    for lp, (x, y, s, info) in zip(lps, res):
+        assert info["status_name"] == "OK", info
+        ox, oy, os_, oinfo = orc.lp_solve_lp(lp, method=2, inner_sweeps=3)
+        assert oinfo["status_name"] == "OK"
+        assert abs(info["obj_primal"] - oinfo["obj_primal"]) <= 1e-7 * abs(oinfo["obj_primal"])
+        pinf, dinf, gap = certs(lp, x, y, s)
+        assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
