@@ -162,33 +162,6 @@ struct GridGrp {
     __syncthreads();
     return *s_ok != 0;
   }
-  // split form: arrive, independent work (prefetch), wait
-  __device__ __forceinline__ void arrive() {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      epoch += 1;
-      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
-    }
-  }
-  __device__ __forceinline__ bool wait(int *s_ok) {
-    if (threadIdx.x == 0) {
-      const unsigned long long target = epoch * (unsigned long long)gridDim.x;
-      int ok = 1;
-      unsigned it = 0;
-      unsigned long long t0 = 0;
-      while (ld_acquire(cnt) < target) {
-        if ((++it & 255u) == 0u) {
-          if (*(volatile int *)status != 0) { ok = 0; break; }
-          unsigned long long now = globaltimer();
-          if (t0 == 0) t0 = now;
-          else if (now - t0 > TIMEOUT_NS) { atomicCAS(status, 0, (int)LPK_TIMEOUT); ok = 0; break; }
-        }
-      }
-      *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-  }
   __device__ __forceinline__ long long barriers() const { return (long long)epoch; }
   __device__ __forceinline__ double uld(int j) const { return __ldcg(u + j); }
   __device__ __forceinline__ void ust(int j, double v) const { u[j] = v; }
@@ -208,16 +181,6 @@ struct ClusterGrp {
   __device__ __forceinline__ bool sync(int *) {
     cg::this_cluster().sync();
     ++epoch;
-    return true;
-  }
-  // split form: the release arrive waits only for this thread's earlier
-  // accesses; loads issued between arrive and wait overlap the barrier
-  __device__ __forceinline__ void arrive() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    ++epoch;
-  }
-  __device__ __forceinline__ bool wait(int *) {
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     return true;
   }
   __device__ __forceinline__ long long barriers() const { return epoch; }
