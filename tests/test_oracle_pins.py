@@ -347,3 +347,17 @@ def test_ls_solve_gives_the_min_norm_direction_of_ne_solve(orc):
     assert info["converged"] and info2["converged"]
     assert np.allclose(dw, dw2, atol=1e-8 * np.linalg.norm(dw))
     assert np.allclose(dw, np.sqrt(d2) * (dense(lp).T @ dy), atol=1e-10 * np.linalg.norm(dw))
+
+
+@pytest.mark.parametrize("method,ell,omega", [(0, 1, 1.4), (1, 3, 0.8), (2, 2, 1.5), (2, 1, 0.6)])
+def test_krylov_solution_does_not_depend_on_the_inner_parameters(orc, method, ell, omega):
+    # ell and omega only change the preconditioner; the minimum-norm solution
+    # of A_hat dw = f is the same (Sec. 3: B = A^T C with C SPD / nonsingular)
+    lp = small_lp(m=18, n=45, density=0.2, seed=14)
+    ahat, Ah = scaled_system(orc, lp, seed=8)
+    nc, color, perm, cptr = orc.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 5)
+    f = Ah @ np.random.default_rng(13).standard_normal(lp.n)
+    dw, dy, info = orc.krylov(method, lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, f, ell, omega,
+                              1e-12, 2000)
+    assert info["converged"]
+    assert np.allclose(dw, np.linalg.pinv(Ah) @ f, atol=1e-8 * np.linalg.norm(dw))
