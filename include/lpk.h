@@ -263,21 +263,23 @@ LPK_API lpk_status lpk_ne_solve(lpk_ctx *ctx, lpk_problem *P, const double *d2, 
                                 double *dw, lpk_krylov_info *kinfo, int32_t on_device);
 
 /* lpk_ne_solve without any device allocation, for callers that cannot call
- * cudaMalloc at solve time (code running while a CUDA graph is captured,
- * applications whose device memory belongs to their own allocator, services
- * that must not hit an out-of-memory error mid-solve).  The paper has no
+ * cudaMalloc while they solve: applications whose device memory belongs to
+ * their own allocator (a caching allocator or a fixed arena), and services
+ * that must not hit an out-of-memory error mid-solve.  The paper has no
  * counterpart: this is a deployment variant of lpk_ne_solve.
- *  - d2[n], f[m], dy[m] and dw[n] (dw may be NULL) must be device pointers.
+ *  - d2[n], f[m], dy[m] and dw[n] (dw may be NULL) must be device memory of
+ *    the context's GPU (or managed memory); anything else is rejected with
+ *    LPK_INVALID_ARG.  Lengths are those of lpk_ne_solve.
  *  - solver LPK_MRNE or LPK_CGNE; always runs the grid path (one CTA per SM).
- *  - All temporaries live in one 32 MiB array reserved in device memory when
- *    the library is loaded (held by every GPU that loads it until exit).  A
- *    problem needing more (about 8 doubles per row and column, plus 260 KB)
- *    is rejected with LPK_INVALID_ARG and a message giving the size.
- *  - The first call on a device looks up that array's address
- *    (cudaGetSymbolAddress); make it before any stream capture.
+ *  - All temporaries live in one 32 MiB array of device memory, reserved when
+ *    the first context on a device is created (lpk_create looks up its
+ *    address) and held by that GPU until the process exits.  A problem
+ *    needing more (about 8 doubles per row and column, plus 260 KB) is
+ *    rejected with LPK_INVALID_ARG and a message giving the size.
  *  - Every call uses the same array and leaves its contents behind: calls
  *    that overlap on the GPU (other streams, other host threads, other
  *    contexts on the same device) race; serialise them.
+ *  - The call is synchronous on the context stream, like lpk_ne_solve.
  *  - Same results as lpk_ne_solve on the grid path (lpk_set_exec). */
 LPK_API lpk_status lpk_ne_solve_noalloc(lpk_ctx *ctx, lpk_problem *P, const double *d2, const double *f,
                                         int32_t inner_sweeps, double omega, int32_t solver,

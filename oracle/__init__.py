@@ -19,6 +19,10 @@ _SRC = os.path.join(_HERE, "lpk_oracle.c")
 _LIB = os.path.join(_HERE, "liblpk_oracle.so")
 
 MRNE, CGNE, ABGMRES = 0, 1, 2
+# per-iteration trace of lp_solve (orc_lp_solve), one row per step k
+TRACE_FIELDS = ("gamma", "mu", "pinf", "dinf", "eps_in", "it_af", "it_cc", "alpha_p", "alpha_d", "sigma",
+                "mu_af", "alpha_p_af", "alpha_d_af", "tau", "failed", "rel_gap")
+TRACE_COLS = len(TRACE_FIELDS)
 STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREAKDOWN",
           6: "EMPTY_ROW_INCONSISTENT", 7: "EMPTY_COL_UNBOUNDED", 8: "INVALID_ARG", 9: "OOM"}
 
@@ -231,7 +235,8 @@ def default_options(**kw) -> Options:
 
 
 def lp_solve(m, n, row_ptr, col_idx, val, b, c, trace=False, **opts):
-    """Algorithm 1.  Returns (x, y, s, info dict[, trace array (iters x 8)])."""
+    """Algorithm 1.  Returns (x, y, s, info dict[, trace array (iters x TRACE_COLS)]);
+    the trace columns are TRACE_FIELDS (see lpk_oracle.h)."""
     o = default_options(**opts)
     args = [_c(row_ptr, np.int64), _c(col_idx, np.int32), _c(val, np.float64), _c(b, np.float64),
             _c(c, np.float64)]
@@ -239,7 +244,7 @@ def lp_solve(m, n, row_ptr, col_idx, val, b, c, trace=False, **opts):
     y = np.empty(m, np.float64)
     s = np.empty(n, np.float64)
     info = Info()
-    tr = np.full((max(o.max_ipm, 1), 8), np.nan) if trace else None
+    tr = np.full((max(o.max_ipm, 1), TRACE_COLS), np.nan) if trace else None
     lib().orc_lp_solve(m, n, *[_p(a) for a in args], C.byref(o), _p(x), _p(y), _p(s), C.byref(info),
                        _p(tr))
     d = info.as_dict()

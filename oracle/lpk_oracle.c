@@ -757,7 +757,8 @@ static int32_t ipm_core(int32_t m, int32_t n, const int64_t *rp, const int32_t *
       dxa[j] = -d2[j] * dsa[j] - x[j];
     }
     double ap = step_len(n, x, dxa, opt->eta), ad = step_len(n, s, dsa, opt->eta);
-    double sigma = 0.0;
+    const double ap_af = ap, ad_af = ad;
+    double sigma = 0.0, muaf_tr = 0.0;
     if (fmin(ap, ad) >= 1.0) {
       memcpy(dx, dxa, sizeof(double) * (size_t)n);
       memcpy(ds, dsa, sizeof(double) * (size_t)n);
@@ -766,6 +767,7 @@ static int32_t ipm_core(int32_t m, int32_t n, const int64_t *rp, const int32_t *
       double muaf = 0.0;
       for (int32_t j = 0; j < n; ++j) muaf += (x[j] + ap * dxa[j]) * (s[j] + ad * dsa[j]);
       muaf /= n;
+      muaf_tr = muaf;
       /* reading: early phase (Gamma >= 1e-3) sigma = min(0.208, (mu_af/mu)^2),
          late phase sigma = min(0.208, 10 Gamma) */
       if (Gam >= 1e-3) {
@@ -862,9 +864,10 @@ static int32_t ipm_core(int32_t m, int32_t n, const int64_t *rp, const int32_t *
     if (failed) info->krylov_failures++;
     failed_prev = failed;
     if (trace && k < opt->max_ipm) {
-      double *tr = trace + (size_t)k * 8;
+      double *tr = trace + (size_t)k * ORC_TRACE_COLS;
       tr[0] = Gam; tr[1] = mu; tr[2] = pinf; tr[3] = dinf; tr[4] = eps_in;
-      tr[5] = it_af; tr[6] = it_cc; tr[7] = ap;
+      tr[5] = it_af; tr[6] = it_cc; tr[7] = ap; tr[8] = ad; tr[9] = sigma; tr[10] = muaf_tr;
+      tr[11] = ap_af; tr[12] = ad_af; tr[13] = tau; tr[14] = failed; tr[15] = gap;
     }
     if (opt->verbose)
       fprintf(stderr, "orc k=%2d Gam=%.3e mu=%.3e pinf=%.2e dinf=%.2e gap=%.2e eps=%.1e it=%d/%d "

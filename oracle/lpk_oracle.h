@@ -147,9 +147,14 @@ int32_t orc_ls_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t
 void orc_default_options(orc_options *o);
 
 /* Interior-point method (Algorithm 1 with the w-recurrence of Sec. 2.2).
- * x[n], y[m], s[n] outputs.  trace (may be NULL) receives 8 doubles per
- * iteration for up to max_ipm iterations: Gamma, mu, pinf, dinf, eps_in,
- * Krylov iterations (predictor), Krylov iterations (corrector), alpha_p. */
+ * x[n], y[m], s[n] outputs.  trace (may be NULL) receives ORC_TRACE_COLS
+ * doubles per iteration k < max_ipm, describing the step from iterate k:
+ * Gamma, mu, pinf, dinf, eps_in, Krylov iterations (predictor), Krylov
+ * iterations (corrector), alpha_p, alpha_d (accepted, after backtracking),
+ * sigma, mu_af (0 when the affine direction was taken), alpha_p and alpha_d
+ * of the affine direction, the backtracking factor tau, 1 if a Krylov solve
+ * of the step did not converge, and the relative gap of iterate k. */
+#define ORC_TRACE_COLS 16
 int32_t orc_lp_solve(int32_t m, int32_t n, const int64_t *row_ptr, const int32_t *col_idx,
                      const double *val, const double *b, const double *c, const orc_options *opt,
                      double *x, double *y, double *s, orc_info *info, double *trace);

@@ -113,6 +113,11 @@ LPK_API lpk_status lpk_create(lpk_ctx **out, int32_t device, void *cuda_stream) 
     delete ctx;
     return LPK_CUDA_ERROR;
   }
+  const lpk_status st = noalloc_setup(ctx);  // scratch of lpk_ne_solve_noalloc on this device
+  if (st != LPK_OK) {
+    delete ctx;
+    return st;
+  }
   *out = ctx;
   return LPK_OK;
 }

@@ -92,6 +92,7 @@ struct KArgs {
   int z_off;                       // byte offsets of the shared-memory blocks (see SmemPlan)
   int gs_off, desc_off, val_off, rs_off, cum_off, col_off;
   int resident;                    // rows of each warp cached in shared memory
+  int short_rows;                  // every row has at most 64 entries (batched row updates)
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
@@ -137,19 +138,22 @@ struct GridGrp {
   double *u;
   __device__ __forceinline__ unsigned rank() const { return blockIdx.x; }
   __device__ __forceinline__ unsigned size() const { return gridDim.x; }
-  // The CTA barrier orders this CTA's writes before thread 0's release-add;
-  // the acquire poll orders every later read after all CTAs' writes.
+  // The CTA barrier orders this CTA's writes before thread 0's acq_rel add;
+  // the add (for the last arriver) or the acquire poll orders every later
+  // read after all CTAs' writes.
   // Returns false if the wait timed out or another CTA reported a failure.
   __device__ __forceinline__ bool sync(int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
       epoch += 1;
       const unsigned long long target = epoch * (unsigned long long)gridDim.x;
-      asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(cnt) : "memory");
+      unsigned long long before;
+      asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(before) : "l"(cnt) : "memory");
       int ok = 1;
       unsigned it = 0;
       unsigned long long t0 = 0;
-      while (ld_acquire(cnt) < target) {
+      // the last CTA to arrive has seen every other arrival: no poll
+      while (before + 1 < target && ld_acquire(cnt) < target) {
         if ((++it & 255u) == 0u) {
           if (*(volatile int *)status != 0) { ok = 0; break; }
           unsigned long long now = globaltimer();
@@ -230,8 +234,11 @@ struct RowPre {
   double g;
 };
 
-// Per-warp sweep state in shared memory.  The rows of color c handled by warp
-// w are r0(c) + gw + j GW (j = 0, 1, ...); they own the slots
+// Per-warp sweep state in shared memory.  Rows are dealt to the GW warps of
+// the group round-robin by sweep position: warp gw takes the positions
+// p = gw (mod GW), so every warp holds ceil(m / GW) rows at most whatever the
+// color sizes (rows of one color commute, so the assignment does not change
+// the sweep's result).  The rows of color c held by warp gw own the slots
 // cum_w[c] + j of the warp's arrays: z (row corrections), the row
 // descriptors (k0, len) -- or, when the rows are resident, (offset in the
 // warp's entry cache, len) --, the row index, and (resident) g_r.  Built once
@@ -282,9 +289,9 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
     const int c = base + lane;
     int cnt = 0, r0 = 0;
     if (c < Z.nc) {
-      r0 = __ldg(A.cptr + c);
-      const int rows = __ldg(A.cptr + c + 1) - r0;
-      cnt = rows > gw ? (rows - gw + GW - 1) / GW : 0;
+      const int c0 = __ldg(A.cptr + c), c1 = __ldg(A.cptr + c + 1);
+      r0 = c0 + ((gw - c0) % GW + GW) % GW;  // first sweep position p >= c0 with p = gw (mod GW)
+      cnt = r0 < c1 ? (c1 - 1 - r0) / GW + 1 : 0;
     }
     int incl = cnt;
 #pragma unroll
@@ -296,7 +303,7 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
       const int first = carry + incl - cnt;
       cw[c] = first;
       for (int j = 0; j < cnt; ++j) {
-        const int r = r0 + gw + j * GW;
+        const int r = r0 + j * GW;
         const int k0 = __ldg(A.rp + r), len = __ldg(A.rp + r + 1) - k0;
         dw[first + j] = make_int2(k0, len);
         rsw[first + j] = r;
@@ -428,6 +435,67 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
   return d;
 }
 
+// Up to four (FP32 values) or two (FP64) short rows (at most 64 entries
+// each) of one color from the row cache: the gathers of all of them are
+// issued before the first reduction and their shuffle reductions are
+// interleaved, so the u-load and FP64-add latencies of the rows overlap
+// instead of adding up.  Each row's arithmetic
+// (entry order, reduction tree) is that of row_update_res, so the result does
+// not depend on the batching.
+template <typename TV, typename GRP>
+__device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, const int *cols, const int2 *dw,
+                                               const double *gsw, double *zw, int s0, int s1, double om,
+                                               bool firstpass, bool lastpass, double *acc) {
+  constexpr int NB = sizeof(TV) == 4 ? 4 : 2, E = 2;  // FP64 values need twice the registers
+  const int lane = threadIdx.x & 31;
+  for (int sb = s0; sb < s1; sb += NB) {
+    int cv[NB][E];
+    double av[NB][E], uv[NB][E], sm[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const int2 kl = sb + k < s1 ? dw[sb + k] : make_int2(0, 0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int t = lane + 32 * e;
+        cv[k][e] = t < kl.y ? cols[kl.x + t] : -1;
+        av[k][e] = t < kl.y ? (double)vals[kl.x + t] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+      for (int e = 0; e < E; ++e) uv[k][e] = cv[k][e] >= 0 ? Gp.uld(cv[k][e]) : 0.0;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      double sk = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+        if (cv[k][e] >= 0) sk += av[k][e] * uv[k][e];
+      sm[k] = sk;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const int sl = sb + k;
+      if (sl < s1) {
+        const double gr = gsw[sl];
+        const double d = om * (gr - sm[k]);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) Gp.ust(cv[k][e], uv[k][e] + d * av[k][e]);
+        if (lane == 0) {
+          const double zn = firstpass ? d : zw[sl] + d;
+          zw[sl] = zn;
+          if (lastpass && acc) *acc += zn * gr;
+        }
+      }
+    }
+  }
+}
+
 // inner_sweeps with every row of the warp resident in shared memory: the only
 // global/distributed accesses of a color phase are the gather and scatter of u.
 template <typename TV, typename GRP>
@@ -451,14 +519,18 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
     const bool firstpass = ps == 0, lastpass = ps == passes - 1;
     for (int cc = 0; cc < nc; ++cc) {
       const int c = backward ? nc - 1 - cc : cc;
-      for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
-        const int2 kl = dw[sl];
-        const double gr = gsw[sl];
-        const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om);
-        if (lane == 0) {
-          const double zn = firstpass ? d : zw[sl] + d;
-          zw[sl] = zn;
-          if (lastpass && acc) *acc += zn * gr;
+      if (A.short_rows) {
+        rows_res_short<TV>(Gp, vals, cols, dw, gsw, zw, cw[c], cw[c + 1], om, firstpass, lastpass, acc);
+      } else {
+        for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
+          const int2 kl = dw[sl];
+          const double gr = gsw[sl];
+          const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om);
+          if (lane == 0) {
+            const double zn = firstpass ? d : zw[sl] + d;
+            zw[sl] = zn;
+            if (lastpass && acc) *acc += zn * gr;
+          }
         }
       }
       if (!(lastpass && cc == nc - 1)) {
@@ -486,73 +558,57 @@ __device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g
   if (A.resident) return inner_sweeps_res<TV>(A, Gp, s_ok, g, ssor, acc, C, Z);
   const TV *a = ahat<TV>(A);
   const int lane = threadIdx.x & 31;
-  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
   const double om = A.omega;
   const int passes = ssor ? 2 * A.ell : A.ell;
   const int nc = A.nc;
-  const int nph = passes * nc;
   double *zw = Z.zw();
   const int2 *dw = Z.dw();
-  const int *cw = Z.cw();
+  const int *cw = Z.cw(), *rsw = Z.rw_rows();
+  const int S = cw[nc];  // rows of this warp
   C.passes += passes;
-  // phase ph = (pass, color); backward passes reverse the color order
-  auto color_of = [&](int ph) {
-    const int ps = ph / nc, cc = ph - ps * nc;
-    return (ssor && (ps & 1)) ? nc - 1 - cc : cc;
+  // The warp's rows in processing order: pass ps visits its slots 0..S-1
+  // (colors ascending) or S-1..0 (backward: colors descending); q counts the
+  // rows over all passes.  The row after the current one is fetched before
+  // the current one is worked on, so its loads overlap.
+  auto slot_of = [&](int q) {
+    const int ps = q / S, i = q - ps * S;
+    return (ssor && (ps & 1)) ? S - 1 - i : i;
   };
-  // this warp's next row at or after (phase ph, index j within the phase):
-  // returns the phase holding it (nph if none) and sets *jj
-  auto next_row = [&](int ph, int j, int *jj) {
-    while (ph < nph) {
-      const int c = color_of(ph);
-      if (cw[c] + j < cw[c + 1]) { *jj = j; return ph; }
-      ++ph;
-      j = 0;
-    }
-    return nph;
-  };
-  auto fetch = [&](int ph, int j, RowPre<TV> &P) {
-    const int c = color_of(ph);
-    const int r = __ldg(A.cptr + c) + gw + j * GW;
-    row_fetch<TV>(A, a, g, r, dw[cw[c] + j], P);
-  };
+  const int Q = passes * S;
   RowPre<TV> cur, nxt;
-  int jn = 0;
-  int phn = next_row(0, 0, &jn);  // phase of the row held in cur
-  if (phn < nph) fetch(phn, jn, cur);
-  int jcur = jn;
-  for (int ph = 0; ph < nph; ++ph) {
-    const int c = color_of(ph);
-    const int ps = ph / nc;
+  if (Q > 0) {
+    const int sl = slot_of(0);
+    row_fetch<TV>(A, a, g, rsw[sl], dw[sl], cur);
+  }
+  int q = 0;
+  for (int ps = 0; ps < passes; ++ps) {
+    const bool backward = ssor && (ps & 1);
     const bool firstpass = ps == 0, lastpass = ps == passes - 1;
-    while (phn == ph) {
-      // issue the loads of the row after this one before working on this one
-      int j2 = 0;
-      const int ph2 = next_row(ph, jcur + 1, &j2);
-      if (ph2 < nph) fetch(ph2, j2, nxt);
-      const double d = row_update<TV>(Gp, A, a, cur, om);
-      if (lane == 0) {
-        const int slot = cw[c] + jcur;
-        const double zn = firstpass ? d : zw[slot] + d;
-        zw[slot] = zn;
-        if (lastpass && acc) *acc += zn * cur.g;
+    for (int cc = 0; cc < nc; ++cc) {
+      const int c = backward ? nc - 1 - cc : cc;
+      const int nrow = cw[c + 1] - cw[c];
+      for (int k = 0; k < nrow; ++k, ++q) {
+        const int sl = slot_of(q);
+        if (q + 1 < Q) {
+          const int s2 = slot_of(q + 1);
+          row_fetch<TV>(A, a, g, rsw[s2], dw[s2], nxt);
+        }
+        const double d = row_update<TV>(Gp, A, a, cur, om);
+        if (lane == 0) {
+          const double zn = firstpass ? d : zw[sl] + d;
+          zw[sl] = zn;
+          if (lastpass && acc) *acc += zn * cur.g;
+        }
+        if (q + 1 < Q) cur = nxt;
       }
-      phn = ph2;
-      jcur = j2;
-      if (ph2 < nph) cur = nxt;
-    }
-    if (ph + 1 < nph || !acc) {
-      if (ph + 1 == nph) break;  // the final barrier comes after the z write-out
-      if (!Gp.sync(s_ok)) return false;
+      if (!(lastpass && cc == nc - 1)) {
+        if (!Gp.sync(s_ok)) return false;
+      }
     }
   }
   // z out to global memory (read by the vector phases after the next barrier)
   __syncwarp();
-  for (int c = 0; c < nc; ++c) {
-    const int r0 = __ldg(A.cptr + c);
-    if (lane == 0)
-      for (int j = 0; cw[c] + j < cw[c + 1]; ++j) A.z[r0 + gw + j * GW] = zw[cw[c] + j];
-  }
+  for (int sl = lane; sl < S; sl += 32) A.z[rsw[sl]] = zw[sl];
   if (!acc) {
     if (!Gp.sync(s_ok)) return false;
   }
@@ -1379,27 +1435,31 @@ cudaError_t prepare_fn(const void *fn) {
 // resident, [g slots] [values] [column indices] of the CTA's rows.
 struct SmemPlan {
   size_t total = 0;
-  int rw = 0, resident = 0;
+  int rw = 0, resident = 0, short_rows = 0;
   int z_off = 0, gs_off = 0, desc_off = 0, val_off = 0, rs_off = 0, cum_off = 0, col_off = 0;
 };
 
-// nonzeros of the busiest CTA when ctas x KWPB warps take the rows color by color
+// nonzeros of the busiest CTA when the rows are dealt round-robin by sweep
+// position to its ctas x KWPB warps
 long long max_cta_entries(const DevProblem &P, int ctas) {
   const int GW = ctas * KWPB;
   std::vector<long long> per(ctas, 0);
-  for (int c = 0; c < P.n_colors; ++c) {
-    const int r0 = P.color_ptr_h[c], r1 = P.color_ptr_h[c + 1];
-    for (int i = 0; i < r1 - r0; ++i) per[(i % GW) / KWPB] += P.rp_h[r0 + i + 1] - P.rp_h[r0 + i];
-  }
+  for (int p = 0; p < P.m; ++p) per[(p % GW) / KWPB] += P.rp_h[p + 1] - P.rp_h[p];
   long long mx = 0;
   for (long long v : per) mx = v > mx ? v : mx;
+  return mx;
+}
+
+int max_row_len(const DevProblem &P) {
+  int mx = 0;
+  for (int p = 0; p < P.m; ++p) mx = std::max(mx, P.rp_h[p + 1] - P.rp_h[p]);
   return mx;
 }
 
 SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident) {
   SmemPlan L;
   const int GW = ctas * KWPB;
-  L.rw = (P.m + GW - 1) / GW + P.n_colors;
+  L.rw = std::max(1, (P.m + GW - 1) / GW);  // rows per warp (round-robin by position)
   size_t off = u_bytes;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -1418,6 +1478,7 @@ SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bo
     const int co = take(sizeof(int) * ent);
     if (off <= SMEM_LIMIT) {
       L.resident = 1;
+      L.short_rows = max_row_len(P) <= 64;
       L.gs_off = gs;
       L.val_off = vo;
       L.col_off = co;
@@ -1430,6 +1491,7 @@ SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bo
 void apply_plan(KArgs &A, const SmemPlan &L) {
   A.rw = L.rw;
   A.resident = L.resident;
+  A.short_rows = L.short_rows;
   A.z_off = L.z_off;
   A.gs_off = L.gs_off;
   A.desc_off = L.desc_off;
@@ -1774,7 +1836,8 @@ lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int 
 // Variant for lpk_ne_solve_noalloc: the same persistent kernel with every
 // buffer carved from caller-supplied device memory (ws), no allocation, no
 // events and no pinned host memory.  ws must hold krylov_scratch_doubles()
-// doubles, 256-byte aligned.
+// doubles and be 8-byte aligned: the blocks carved from it are arrays of
+// doubles and the control block, all read and written one element at a time.
 // ---------------------------------------------------------------------------
 size_t krylov_scratch_doubles(const DevProblem &P) {
   const size_t m = P.m > 0 ? P.m : 1, n = P.n > 0 ? P.n : 1;

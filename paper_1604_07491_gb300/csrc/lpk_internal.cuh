@@ -209,6 +209,8 @@ lpk_status krylov_solve(lpk_ctx *ctx, DevProblem &P, int method, int precision, 
                         KrylovResult *out, double *hist);
 lpk_status sweep_only(lpk_ctx *ctx, DevProblem &P, int kind, int precision, int ell, double omega,
                       const double *g_hat, double *z, double *u);
+// address of the no-allocation scratch on ctx->device (lpk_create, once per device)
+lpk_status noalloc_setup(lpk_ctx *ctx);
 // persistent Krylov solve on caller-supplied device memory (no allocation)
 size_t krylov_scratch_doubles(const DevProblem &P);
 // BA-GMRES with NR-SOR on min ||A_hat^T dy_hat - r|| (r_n: n-space, kept

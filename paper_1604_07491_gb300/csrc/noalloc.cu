@@ -1,17 +1,19 @@
 // noalloc.cu -- lpk_ne_solve_noalloc: the search-direction solve without any
 // device allocation.
 //
-// Some callers cannot call cudaMalloc at solve time: code that runs while a
-// CUDA graph is being captured (a plain cudaMalloc is not allowed there),
-// applications whose device memory is owned by their own allocator and must
-// not be taken from the driver behind its back, and long-running services
-// that must not fail with an out-of-memory error in the middle of a solve.
-// For them every temporary of this solve (the internal copies of d2, f, dy,
-// dw, the Krylov workspace, the persistent kernel's control block and its
-// reduction partials) lives in one file-scope device array of fixed size,
-// reserved when the library is loaded and held by every GPU that loads it
-// until the process exits.
+// Some callers cannot call cudaMalloc while they solve: applications whose
+// device memory is owned by their own allocator (a caching allocator or a
+// fixed arena that must not lose memory to the driver behind its back), and
+// long-running services that must not fail with an out-of-memory error in the
+// middle of a solve.  For them every temporary of this solve (the internal
+// copies of d2, f, dy, dw, the Krylov workspace, the persistent kernel's
+// control block and its reduction partials) lives in one file-scope device
+// array of fixed size.  Its address is looked up when the first context on a
+// device is created (lpk_create), which also loads this module on that device
+// under lazy module loading, so the array is reserved then and held by that
+// GPU until the process exits.
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "lpk_internal.cuh"
@@ -31,25 +33,43 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 namespace {
 
 double *g_scratch_dev[MAX_DEVICES] = {nullptr};  // device address per device, set once
+std::mutex g_scratch_mu;
 
-// Set-up, once per device, with that device current (the entry point calls
-// cudaSetDevice(ctx->device) first).
+}  // namespace
+
+// Set-up, once per device, with that device current: lpk_create calls it
+// right after cudaSetDevice(device).  cudaGetSymbolAddress gives the device
+// address of the array (the name itself is only a host-side stand-in) and
+// loads the module, reserving the array, if that has not happened yet.
+lpk_status noalloc_setup(lpk_ctx *ctx) {
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= MAX_DEVICES) return LPK_OK;  // no scratch on such a device: the entry point says so
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (g_scratch_dev[dev]) return LPK_OK;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    ctx->err = std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? LPK_OOM : LPK_CUDA_ERROR;
+  }
+  g_scratch_dev[dev] = (double *)p;
+  return LPK_OK;
+}
+
+namespace {
+
 lpk_status scratch_address(lpk_ctx *ctx, double **out) {
   const int dev = ctx->device;
-  if (dev < 0 || dev >= MAX_DEVICES) {
-    ctx->err = "lpk_ne_solve_noalloc: device index out of range";
+  double *p = nullptr;
+  if (dev >= 0 && dev < MAX_DEVICES) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    p = g_scratch_dev[dev];
+  }
+  if (!p) {
+    ctx->err = "lpk_ne_solve_noalloc: no scratch array on this device (device index beyond 63?)";
     return LPK_INVALID_ARG;
   }
-  if (!g_scratch_dev[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      ctx->err = std::string("lpk_ne_solve_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
-      return LPK_CUDA_ERROR;
-    }
-    g_scratch_dev[dev] = (double *)p;
-  }
-  *out = g_scratch_dev[dev];
+  *out = p;
   return LPK_OK;
 }
 
@@ -62,13 +82,15 @@ __global__ void k_d2_flag(int n, const double *d2, double *flag) {
   if (j < n && !(d2[j] > 0.0 && isfinite(d2[j]))) flag[0] = 1.0;
 }
 
-bool is_device_ptr(const void *p) {
+// device memory of the context's GPU, or managed memory
+bool is_device_ptr(const void *p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 size_t round4(size_t x) { return (x + 3) & ~size_t(3); }  // keep 32-byte alignment of each block
@@ -91,8 +113,9 @@ LPK_API lpk_status lpk_ne_solve_noalloc(lpk_ctx *ctx, lpk_problem *P, const doub
     ctx->err = "lpk_ne_solve_noalloc: invalid arguments (solver must be MRNE or CGNE)";
     return LPK_INVALID_ARG;
   }
-  if (!is_device_ptr(d2) || !is_device_ptr(f) || !is_device_ptr(dy) || (dw && !is_device_ptr(dw))) {
-    ctx->err = "lpk_ne_solve_noalloc: d2, f, dy and dw must be device pointers";
+  const int dv = ctx->device;
+  if (!is_device_ptr(d2, dv) || !is_device_ptr(f, dv) || !is_device_ptr(dy, dv) || (dw && !is_device_ptr(dw, dv))) {
+    ctx->err = "lpk_ne_solve_noalloc: d2, f, dy and dw must be device (or managed) memory of the context's GPU";
     return LPK_INVALID_ARG;
   }
   const size_t m = d.m, n = d.n;

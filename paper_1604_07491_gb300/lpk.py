@@ -376,7 +376,19 @@ class Problem:
     def ne_solve_noalloc(self, d2, f, dy, dw=None, inner_sweeps=1, omega=1.0, solver=MRNE,
                          precision=FP64, tol=1e-10, max_iter=0):
         """lpk_ne_solve_noalloc: device tensors in and out (dy, dw preallocated by
-        the caller); the library allocates nothing.  Returns the info dict."""
+        the caller); the library allocates nothing.  Returns the info dict.
+        The C call takes no lengths, so the tensors are checked here: float64,
+        contiguous, on the context's GPU, d2/dw of n entries and f/dy of m."""
+        import torch
+        for name, t, size in (("d2", d2, self.n), ("f", f, self.m), ("dy", dy, self.m), ("dw", dw, self.n)):
+            if t is None and name == "dw":
+                continue
+            if not (_is_torch(t) and t.is_cuda and t.device.index == self.ctx.device):
+                raise ValueError(f"{name} must be a CUDA tensor on device {self.ctx.device}")
+            if t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous float64 tensor")
+            if t.numel() < size:
+                raise ValueError(f"{name} has {t.numel()} entries, needs {size}")
         ki = KrylovInfo()
         _check(self.ctx.handle, load().lpk_ne_solve_noalloc(
             self.ctx.handle, self._h, _ptr(d2)[0], _ptr(f)[0], inner_sweeps, omega, solver, precision,

@@ -1,11 +1,12 @@
 """lpk_ne_solve_noalloc: the search-direction solve for callers that cannot
-allocate device memory at solve time (for instance while a CUDA graph is being
-captured).  Its temporaries live in a fixed device array the library reserves
-at load time.  The test calls it through the C ABI and checks it against the
-allocating lpk_ne_solve on the same path, twice in a row (the shared array
-keeps the previous call's contents), and checks that an oversized problem is
-rejected with a clear error.  Collected last so that a stop at the first
-failure has run every other test."""
+call cudaMalloc while they solve (applications whose device memory belongs to
+their own allocator, services that must not run out of memory mid-solve).  Its
+temporaries live in a fixed device array reserved when the first context on a
+device is created.  The test calls it through the C ABI and checks it against
+the allocating lpk_ne_solve on the same path, twice in a row (the shared array
+keeps the previous call's contents), and checks that an oversized problem, host
+memory and badly typed or short tensors are rejected with a clear error.
+Collected last so that a stop at the first failure has run every other test."""
 import numpy as np
 import pytest
 
@@ -66,5 +67,34 @@ def test_noalloc_rejects_oversized_problem(lpk):
     with pytest.raises(lpk.LpkError) as e:
         P.ne_solve_noalloc(d2, f, dy)
     assert e.value.status == lpk.INVALID_ARG and "MiB" in str(e.value)
+    P.free()
+    ctx.close()
+
+
+def test_noalloc_rejects_bad_buffers(lpk):
+    """Host memory is refused by the C entry point; the binding refuses
+    tensors of the wrong type or length before the call (the C call takes
+    no lengths)."""
+    import ctypes as C
+    lp = gen.tiny_lp()
+    ctx = lpk.Context(0)
+    P = lpk.Problem.from_lp(ctx, lp, device="cuda")
+    d2 = torch.ones(lp.n, dtype=torch.float64, device="cuda")
+    f = torch.ones(lp.m, dtype=torch.float64, device="cuda")
+    dy = torch.empty(lp.m, dtype=torch.float64, device="cuda")
+    host_d2 = np.ones(lp.n)
+    ki = lpk.KrylovInfo()
+    st = lpk.load().lpk_ne_solve_noalloc(ctx.handle, P._h, C.c_void_p(host_d2.ctypes.data),
+                                         C.c_void_p(f.data_ptr()), 1, 1.0, lpk.MRNE, lpk.FP64, 1e-8, 0,
+                                         C.c_void_p(dy.data_ptr()), None, C.byref(ki))
+    assert st == lpk.INVALID_ARG and "device" in ctx.last_error()
+    with pytest.raises(ValueError):
+        P.ne_solve_noalloc(d2.float(), f, dy)
+    with pytest.raises(ValueError):
+        P.ne_solve_noalloc(d2, f, dy[: lp.m - 1])
+    with pytest.raises(ValueError):
+        P.ne_solve_noalloc(d2.cpu(), f, dy)
+    info = P.ne_solve_noalloc(d2, f, dy, tol=1e-10)
+    assert info["converged"]
     P.free()
     ctx.close()
