@@ -1,17 +1,29 @@
-"""Benchmark: LPs solved per second (and per-LP latency) on seeded synthetic
-workloads, through the C ABI.
+"""Benchmark of the search-direction hot path through the C ABI, on seeded
+synthetic workloads.
 
-A step is one batch: B LPs of the workload family (different seeds), each a
-complete interior-point solve (Algorithm 1 with the Krylov search-direction
-solves), run side by side on the GPU (lpk_lp_solve_batch: one context, stream
-and thread-block cluster per LP).  --batch 1 times one LP at a time on the
-autotuned single-LP path.  Inputs are resident in HBM when the timed region
-starts.  Prints one JSON line (rank 0).  The serving workload (--workload
-serving) replays the Poisson stream through the continuous-batching server.
+Default (--workload large): the large power-law LP (m = 150,000, n = 434,580,
+mean column degree 6, maximum 400, 406 colors).  A step is one lpk_sweep call
+(D-scaling and row scaling of Sec. 3.5, then one NE-SOR pass of Algorithm 6
+over the FP32 copy of the scaled matrix, mixed precision) followed by one
+FP64 product y = A x (lpk_spmv); the value is the NE-sweep bandwidth: the
+algorithmic bytes of one NE-SOR pass (the FP32 sweep formula of the scope
+table, half of an NE-SSOR sweep) divided by the sweep kernel's CUDA-event
+duration, measured live on the launching stream.  The L2 is flushed (256 MB
+written) between timed steps.  The same line carries, as secondary keys, the
+LP throughput of the degenerate assignment LP (lp_solve: a batch of LPs
+solved side by side in mixed precision to gap <= 1e-8, against plain FP64 one
+LP at a time) and the first interior-point iterations of the large LP itself
+(large_solve), which the paper's method does not bring to gap <= 1e-8 within
+its Krylov cap on this family.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
-                  [--workload assignment|tiny|medium|medium_0.1|serving]
-                  [--precision mixed|fp64] [--solver mrne|cgne|abgmres]
+Other workloads: --workload assignment|tiny|medium|medium_0.1 time complete
+LP solves (a step = a batch of LPs, LPs/s); --workload serving replays the
+Poisson stream through the continuous-batching server; --workload large_x8
+measures the sparse products on the large matrix replicated 8x (larger than
+L2).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload W]
+                  [--batch B] [--precision mixed|fp64] [--solver mrne|cgne|abgmres]
                   [--impl lpk|reference]
 """
 from __future__ import annotations
@@ -36,11 +48,15 @@ os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "LPs solved/s & p99 latency at gap≤1e-8 (mixed vs FP64); NE-sweep HBM GB/s"
 UNIT = "LPs/s"
+METRIC_SWEEP = METRIC   # the large LP's line reports the NE-sweep part (unit GB/s)
 SOLVERS = {"mrne": 0, "cgne": 1, "abgmres": 2}
 
 # workload -> generator options and LPs per step.  max_krylov 40000 is the
 # relaxed Krylov cap the paper uses for difficult problems (Sec. 4.2).
 WORKLOADS = {
+    "large": dict(desc="large sparse LP m=150000 n=434580, power-law column degrees (mean 6, max 400), N(0,1), "
+                       "x0/y0/s0 construction; NE-SOR sweep + FP64 SpMV, mixed precision",
+                  opts=dict(solver=2, inner_sweeps=1, omega=1.0, max_krylov=40000), batch=1),
     "medium": dict(desc="rank-deficient sparse LP m=20000 n=60000, 8 nnz/col N(0,1), 1% dependent rows",
                    opts=dict(solver=0, inner_sweeps=5, omega=1.0, max_krylov=40000), batch=1),
     "assignment": dict(desc="degenerate assignment LP k=14 (n=38416, m=588), costs U{0..100}",
@@ -58,6 +74,8 @@ WORKLOADS = {
 
 def make_lp(workload, seed_offset=0):
     from paper_1604_07491_gb300 import gen
+    if workload == "large":
+        return gen.large_lp(1.0)
     if workload == "medium":
         return gen.medium_lp(1.0, seed=gen.SEED_BASE + 2 + 1000 * seed_offset)
     if workload == "medium_0.1":
@@ -149,6 +167,53 @@ def algorithmic_bytes(stats, m, n, nnz, precision):
             + stats.get("basis_passes", 0) * 8 * m)
 
 
+def sweep_pass_bytes(nnz, m):
+    """Algorithmic bytes of one NE-SOR pass over the FP32 copy of the scaled
+    matrix, by the FP32 sweep formula of the scope table (half of its NE-SSOR
+    sweep): per nonzero the value and column index (4 + 4 B) and one read and
+    one write of the gathered/scattered u entry (4 + 4 B); per row the row
+    pointer (8 B), g (4 B) and the z read-modify-write (8 B)."""
+    return nnz * 16 + m * 20
+
+
+def sweep_pass_bytes_moved(nnz, m):
+    """The same pass with u kept in FP64, as this implementation does (its
+    u gather and scatter move 8 + 8 B per nonzero)."""
+    return nnz * 24 + m * 20
+
+
+def spmv_bytes(nnz, m, n):
+    """FP64 y = A x by the scope table's formula: value and column index
+    (8 + 4 B) per nonzero, row pointer and result (8 + 8 B) per row, x read
+    once (8 B per column)."""
+    return nnz * 12 + m * 16 + n * 8
+
+
+def source_digest(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel_key):
+    """DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+    a kernel from the committed ncu record (profiles/ncu_traffic.json), or
+    None when the record is missing or the kernel's sources changed since the
+    capture (the record stores the SHA-256 of the sources it was taken on)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None, "no ncu record"
+    rec = json.load(open(path)).get(kernel_key)
+    if not rec:
+        return None, "no ncu record for this kernel"
+    if rec.get("sources_sha256") != source_digest(rec["sources"]):
+        return None, "kernel sources changed since the ncu capture"
+    return float(rec["dram_bytes_per_launch"]), rec.get("command", "")
+
+
 def replica_offsets(rank, batch):
     """Seed offsets of the LPs rank `rank` solves: replicas are independent
     units (weak scaling), every rank gets its own LPs of the family."""
@@ -230,10 +295,70 @@ def oracle_throughput(workload, opts, count, seed_base=0, pool=None, max_ipm=0):
 # ---------------------------------------------------------------------------
 # reference arm: the oracle as it stands, on the host cores
 # ---------------------------------------------------------------------------
+def oracle_sweep_rate(lp, passes, warmup=1):
+    """The oracle's NE-SOR pass (plain C, FP64, one thread) on the large LP's
+    scaled matrix: (GB/s by the same byte formula as the GPU arm, seconds per
+    pass, sample text).  The matrix is scaled once, outside the timing."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    d2, g, _ = large_inputs(lp)
+    nc, col, perm, cptr = oracle.color_rows(lp.m, lp.n, lp.row_ptr, lp.col_idx, 0x5EED)
+    ahat, rho = oracle.scale_rows(lp.m, lp.row_ptr, lp.col_idx, lp.val, d2)
+    for _ in range(warmup):   # g is in the scaled space, as lpk_sweep takes it
+        oracle.nesor(lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, g, 1, 1.0)
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        oracle.nesor(lp.m, lp.n, lp.row_ptr, lp.col_idx, ahat, perm, g, 1, 1.0)
+    sec = (time.perf_counter() - t0) / passes
+    gbs = sweep_pass_bytes(lp.nnz, lp.m) / sec / 1e9
+    sample = (f"{passes} NE-SOR passes (Algorithm 6, ell = 1) of the oracle (single-threaded C, FP64) over the "
+              f"large LP's scaled matrix (m={lp.m}, n={lp.n}, nnz={lp.nnz}, {nc} colors), {sec:.3f} s per pass, "
+              f"after {warmup} untimed pass(es)")
+    return gbs, sec, sample
+
+
+def large_inputs(lp):
+    """Seeded inputs of the large-LP sweep benchmark: d2 = x/s spread over
+    e^[-4, 4], g ~ N(0, 1), x ~ N(0, 1) for the product."""
+    import numpy as np
+    rng = np.random.default_rng(20160407 + 4)
+    return np.exp(rng.uniform(-4.0, 4.0, lp.n)), rng.standard_normal(lp.m), rng.standard_normal(lp.n)
+
+
+def run_reference_large(args, wl):
+    from paper_1604_07491_gb300 import gen
+    lp = gen.large_lp(1.0)
+    vals, samples = [], []
+    for i in range(args.warmup + args.steps):
+        gbs, sec, sample = oracle_sweep_rate(lp, passes=1, warmup=0)
+        if i >= args.warmup:
+            vals.append(gbs)
+            samples.append(sample)
+    val = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC_SWEEP, "value": val, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sweep_pass_bytes(lp.nnz, lp.m) / (val * 1e9),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": large_config(lp, None, "mixed"),
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": samples[-1]},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def large_config(lp, n_colors, precision):
+    return {"workload": f"large: {WORKLOADS['large']['desc']}", "m": lp.m, "n": lp.n, "nnz": lp.nnz,
+            "n_colors": n_colors, "precision": precision, "sweep": "NE-SOR (Algorithm 6), ell = 1, omega = 1",
+            "inputs": "d2 = exp(U(-4, 4)), g ~ N(0,1), x ~ N(0,1) (seeded), resident in HBM",
+            "l2": "256 MB buffer written between timed steps", "parallelism": "replicas"}
+
+
 def run_reference(args, wl, opts):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "large":
+        return run_reference_large(args, wl)
     B = args.batch if args.batch > 0 else wl["batch"]
     # serving and medium LPs take the oracle minutes each: one interior-point
     # iteration per LP bounds a step there (said in the sample text)
@@ -256,11 +381,21 @@ def run_reference(args, wl, opts):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * B / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {wl['desc']}", "batch": B, **opts},
+            "config": reference_config(args, wl, opts, B),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": samples[-1]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def reference_config(args, wl, opts, B):
+    """The GPU arm's config keys for the same workload (the oracle runs FP64
+    whatever the GPU arm's precision; the precision key names the GPU arm's)."""
+    lp0 = make_lp(args.workload, 0)
+    return {"workload": f"{args.workload}: {wl['desc']}", "m": lp0.m, "n": lp0.n, "nnz": lp0.nnz,
+            "batch": B, "global_batch": B * args.gpus, "precision": args.precision,
+            "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]], "inner_sweeps": opts["inner_sweeps"],
+            "omega": opts.get("omega", 1.0), "max_krylov": opts.get("max_krylov", 0)}
 
 
 # ---------------------------------------------------------------------------
@@ -275,13 +410,6 @@ def sum_stats(ctxs):
             else:
                 tot[k] = tot.get(k, 0) + v
     return tot
-
-
-# DRAM bytes (read + write) of one persistent Krylov launch, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the same workload and
-# kernel; the working set is L2-resident, so it is the first touch of the
-# matrix and does not grow with the launch's length
-MEASURED_TRAFFIC = {("assignment", "mixed", 2): 3.61e6}
 
 
 def roofline(stats, lp, precision, makespan_ms, traffic=None):
@@ -304,7 +432,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lpk", choices=["lpk", "reference"])
-    ap.add_argument("--workload", default="assignment", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="LPs per step solved side by side (0: workload's)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cluster", type=int, default=0, choices=[0, 4, 8, 16],
@@ -319,6 +447,10 @@ def main():
     ap.add_argument("--lanes", type=int, default=16, help="serving: server lanes")
     ap.add_argument("--serving-max-m", type=int, default=0,
                     help="serving: replay only the stream's LPs with m <= this (0: all)")
+    ap.add_argument("--lp-steps", type=int, default=2,
+                    help="large: timed steps of the assignment-LP solve throughput (0: skip)")
+    ap.add_argument("--large-ipm", type=int, default=6,
+                    help="large: interior-point iterations of the large LP run once (0: skip)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     opts = dict(wl["opts"])
@@ -349,7 +481,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    if args.workload == "serving":
+    if args.workload == "large":
+        line = run_large(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist)
+    elif args.workload == "serving":
         line = run_serving(args, wl, opts, lpk, local, rank, world, barrier)
     elif args.workload == "large_x8":
         line = run_bandwidth(args, wl, lpk, torch, dev, local, rank, world, barrier)
@@ -359,6 +493,132 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_large(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist):
+    """The default line: NE-sweep and SpMV bandwidth on the large LP, plus the
+    assignment LP's solve throughput and the large LP's first interior-point
+    iterations as secondary keys."""
+    import numpy as np
+    from paper_1604_07491_gb300 import gen
+    lp = gen.large_lp(1.0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = lpk.Context(local, stream.cuda_stream)
+    P = lpk.Problem.from_lp(ctx, lp, device=dev)
+    d2_h, g_h, x_h = large_inputs(lp)
+    d2, g, x = (torch.from_numpy(v).to(dev) for v in (d2_h, g_h, x_h))
+    prec = lpk.MIXED if args.precision == "mixed" else lpk.FP64
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    bsw, bsp = sweep_pass_bytes(lp.nnz, lp.m), spmv_bytes(lp.nnz, lp.m, lp.n)
+
+    def step(d2v, gv, xv):
+        P.sweep(d2v, gv, kind=lpk.NE_SOR, inner_sweeps=1, omega=1.0, precision=prec)
+        return P.spmv(xv)
+
+    for _ in range(args.warmup):
+        step(d2, g, x)
+    torch.cuda.synchronize(dev)
+    ctx.reset_stats()
+    step_ms, spmv_ms = [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            barrier()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            P.sweep(d2, g, kind=lpk.NE_SOR, inner_sweeps=1, omega=1.0, precision=prec)
+            e1.record(stream)
+            P.spmv(x)
+            e2.record(stream)
+            barrier()
+            step_ms.append(e0.elapsed_time(e2))
+            spmv_ms.append(e1.elapsed_time(e2))
+    st = ctx.stats()
+    sweep_ms = st["krylov_ms"] / max(1, st["krylov_launches"])     # the sweep kernel alone (library events)
+    sweep_ms = max_over_ranks(sweep_ms, dist, dev)
+    spmv_med = max_over_ranks(statistics.median(spmv_ms), dist, dev)
+    gbs = world * bsw / (sweep_ms / 1e3) / 1e9
+    gbs_spmv = world * bsp / (spmv_med / 1e3) / 1e9
+    hbm, src = peaks()
+    traffic, traffic_src = measured_traffic("sweep_large_mixed")
+    launches = st["launches"]
+
+    # end to end through the C ABI with host buffers (copies inside the timing)
+    out_z, out_u, out_y = np.empty(lp.m), np.empty(lp.n), np.empty(lp.m)
+    e2e_s = []
+    for i in range(3):
+        barrier()
+        t0 = time.perf_counter()
+        P.sweep(d2_h, g_h, kind=lpk.NE_SOR, inner_sweeps=1, omega=1.0, precision=prec)
+        P.spmv(x_h)
+        t1 = time.perf_counter()
+        if i:
+            e2e_s.append(t1 - t0)
+    e2e = {"value": world * bsw / statistics.median(e2e_s) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": int(d2_h.nbytes + g_h.nbytes + x_h.nbytes),
+           "d2h_bytes_per_step": int(out_z.nbytes + out_u.nbytes + out_y.nbytes),
+           "what": "lpk_sweep + lpk_spmv on host arrays: host-to-device copies of d2, g, x and device-to-host "
+                   "copies of z, u, y inside the timing; value = the sweep's algorithmic bytes / wall time"}
+
+    # the large LP's first interior-point iterations (the method stalls later on this family)
+    large_solve = None
+    if args.large_ipm > 0:
+        b, c = torch.from_numpy(lp.b).to(dev), torch.from_numpy(lp.c).to(dev)
+        ctx.reset_stats()
+        t0 = time.perf_counter()
+        xs, ys, ss, info = P.lp_solve(b, c, precision=prec, max_ipm=args.large_ipm, **opts)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        st2 = ctx.stats()
+        large_solve = {"max_ipm": args.large_ipm, "seconds": wall, "status": info["status_name"],
+                       "ipm_iters": info["ipm_iters"], "krylov_iters": info["krylov_iters_total"],
+                       "gamma": info["gamma"], "rel_gap": info["rel_gap"], "pinf": info["pinf"],
+                       "dinf": info["dinf"], "ms_per_krylov_iter": st2["krylov_ms"] / max(1, st2["krylov_iters"]),
+                       "solver": ["MRNE", "CGNE", "AB-GMRES"][opts["solver"]], "inner_sweeps": opts["inner_sweeps"]}
+    P.free()
+    ctx.close()
+
+    # the assignment LP's solve throughput: batched mixed vs FP64 one LP at a time
+    lp_solve = None
+    if args.lp_steps > 0:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.steps, sub.batch = "assignment", args.lp_steps, 0
+        sub.cpu_baseline = args.cpu_baseline
+        aw = WORKLOADS["assignment"]
+        r = run_batch(sub, aw, dict(aw["opts"]), lpk, torch, dev, local, rank, world, barrier, dist)
+        if r is not None:
+            lp_solve = {k: r[k] for k in ("value", "unit", "ms_per_step", "p50_ms", "p99_ms", "solve", "fp64",
+                                          "e2e", "cpu_baseline", "roofline", "config", "clocks", "gpu_launches")}
+            lp_solve["steps"], lp_solve["warmup"] = sub.steps, sub.warmup
+
+    if rank != 0:
+        return None
+    cpu = None
+    if args.cpu_baseline and world == 1:
+        v, sec, sample = oracle_sweep_rate(lp, passes=3)
+        cpu = {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample, "seconds_per_pass": sec}
+    return {
+        "metric": METRIC_SWEEP, "value": gbs, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 values / f64 accumulation" if prec == lpk.MIXED else "f64", "data": "synthetic",
+        "config": large_config(lp, P.n_colors, args.precision),
+        "value_is": "NE-sweep bandwidth: algorithmic bytes of one NE-SOR pass / sweep-kernel time (LPs/s of the "
+                    "metric's first part: lp_solve)",
+        "sweep": {"ms": sweep_ms, "bytes": bsw, "bytes_moved_fp64_u": sweep_pass_bytes_moved(lp.nnz, lp.m),
+                  "gbs": gbs, "frac": gbs / hbm / world, "colors": P.n_colors,
+                  "us_per_color_phase": 1e3 * sweep_ms / max(1, P.n_colors)},
+        "spmv": {"ms": spmv_med, "bytes": bsp, "gbs": gbs_spmv, "frac": gbs_spmv / hbm / world,
+                 "what": "lpk_spmv y = A x in FP64 incl. the gather/scatter between input and internal numbering"},
+        "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": hbm, "unit": "GB/s", "frac": gbs / world / hbm,
+                     "traffic": traffic, "traffic_source": traffic_src,
+                     "kernel": "k_krylov<M_SWEEP, float, GridGrp> (one NE-SOR pass, grid path, rows cached in "
+                               "shared memory)",
+                     "peak_source": f"{src} hbm_gbs", "avg_launch_ms": sweep_ms, "bytes_per_launch": bsw,
+                     "launches": st["krylov_launches"]},
+        "lp_solve": lp_solve, "large_solve": large_solve,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
 
 
 def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist):
@@ -491,7 +751,7 @@ def run_batch(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
                   "max_dinf": max(d["dinf"] for d in infos)},
         "fp64": fp64,
         "roofline": roofline(stats, lp0, args.precision, total_ms,
-                             MEASURED_TRAFFIC.get((args.workload, args.precision, opts["solver"]))),
+                             measured_traffic(f"krylov_{args.workload}_{args.precision}")[0]),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": stats["launches"], "clocks": clk.summary(),
     }
 

@@ -201,6 +201,18 @@ LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out);
 LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx);
 LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size);
 
+/* Failure detection of the grid path (the paper has no counterpart).  Every
+ * wait of the persistent kernel's software grid barrier is bounded by
+ * `seconds` of %globaltimer (default 5; must be > 0): when it runs out, the
+ * CTA records LPK_TIMEOUT, every CTA leaves the kernel at its next barrier,
+ * and the call returns LPK_TIMEOUT with the context still usable.
+ * test_stall_barrier (testing only, 0 = off): in each grid-path launch, CTA 0
+ * withholds its arrival at the grid barrier with that number (counted from 1
+ * in the launch), so every wait on it runs out; this is how the timeout path
+ * is exercised without faulting the GPU.  The cluster path's hardware
+ * barriers have no software wait and are not affected. */
+LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier);
+
 /* Copy A to the device, validate it, remove empty rows and columns (the only
  * preprocessing of Sec. 4.2) and compute the multicolor row order on the
  * device: rows are colored greedily in decreasing priority

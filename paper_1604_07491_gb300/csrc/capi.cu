@@ -168,6 +168,17 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
   return LPK_OK;
 }
 
+LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier) {
+  if (!ctx) return LPK_INVALID_ARG;
+  if (!(seconds > 0.0 && seconds < 1e6) || test_stall_barrier < 0) {
+    ctx->err = "lpk_set_wait_limit: seconds must be in (0, 1e6) and test_stall_barrier >= 0";
+    return LPK_INVALID_ARG;
+  }
+  ctx->wait_limit_ns = (unsigned long long)(seconds * 1e9);
+  ctx->stall_barrier = test_stall_barrier;
+  return LPK_OK;
+}
+
 LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx) {
   if (!ctx) return LPK_INVALID_ARG;
   ctx->stats = lpk_stats{};

@@ -55,7 +55,6 @@ constexpr int KTPB = 256;
 constexpr int KWPB = KTPB / 32;
 constexpr int RC = 4;                 // row entries per lane kept in registers
 constexpr int RCR = 8;                // same, rows cached in shared memory
-constexpr unsigned long long TIMEOUT_NS = 5000000000ull;  // 5 s per barrier wait
 constexpr int MAX_CLUSTER = 16;
 constexpr int MAX_SHIFT = 14;         // <= 2^14 doubles (128 KB) of u per CTA
 
@@ -93,6 +92,8 @@ struct KArgs {
   int gs_off, desc_off, val_off, rs_off, cum_off, col_off;
   int resident;                    // rows of each warp cached in shared memory
   int short_rows;                  // every row has at most 64 entries (batched row updates)
+  unsigned long long timeout_ns;   // grid path: bound of every barrier wait
+  unsigned long long stall_barrier;  // grid path, testing: barrier CTA 0 does not arrive at (0: none)
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
@@ -136,6 +137,8 @@ struct GridGrp {
   int *status;
   unsigned long long epoch;
   double *u;
+  unsigned long long timeout_ns;  // bound of every wait
+  unsigned long long stall;       // testing: CTA 0 does not arrive at this barrier (0: none)
   __device__ __forceinline__ unsigned rank() const { return blockIdx.x; }
   __device__ __forceinline__ unsigned size() const { return gridDim.x; }
   // The CTA barrier orders this CTA's writes before thread 0's acq_rel add;
@@ -147,8 +150,14 @@ struct GridGrp {
     if (threadIdx.x == 0) {
       epoch += 1;
       const unsigned long long target = epoch * (unsigned long long)gridDim.x;
-      unsigned long long before;
-      asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(before) : "l"(cnt) : "memory");
+      unsigned long long before = 0;
+      if (epoch == stall && blockIdx.x == 0) {
+        // testing: withhold this CTA's arrival so that every wait on this
+        // barrier runs out (each wait below is bounded by timeout_ns)
+        __threadfence();
+      } else {
+        asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], 1;" : "=l"(before) : "l"(cnt) : "memory");
+      }
       int ok = 1;
       unsigned it = 0;
       unsigned long long t0 = 0;
@@ -158,7 +167,7 @@ struct GridGrp {
           if (*(volatile int *)status != 0) { ok = 0; break; }
           unsigned long long now = globaltimer();
           if (t0 == 0) t0 = now;
-          else if (now - t0 > TIMEOUT_NS) { atomicCAS(status, 0, (int)LPK_TIMEOUT); ok = 0; break; }
+          else if (now - t0 > timeout_ns) { atomicCAS(status, 0, (int)LPK_TIMEOUT); ok = 0; break; }
         }
       }
       *s_ok = ok;
@@ -457,10 +466,17 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int t = lane + 32 * e;
-        cv[k][e] = t < kl.y ? cols[kl.x + t] : -1;
-        av[k][e] = t < kl.y ? (double)vals[kl.x + t] : 0.0;
+        cv[k][e] = -1;
+        av[k][e] = 0.0;
+        if (t < kl.y) {
+          cv[k][e] = cols[kl.x + t];
+          av[k][e] = (double)vals[kl.x + t];
+        }
       }
     }
+    // rows of this batch (warp-uniform): FP64 work is spent on them only, an
+    // FP64 warp instruction being costly on this GPU
+    const int nb = min(NB, s1 - sb);
 #pragma unroll
     for (int k = 0; k < NB; ++k)
 #pragma unroll
@@ -468,15 +484,18 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       double sk = 0.0;
+      if (k < nb) {
 #pragma unroll
-      for (int e = 0; e < E; ++e)
-        if (cv[k][e] >= 0) sk += av[k][e] * uv[k][e];
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) sk += av[k][e] * uv[k][e];
+      }
       sm[k] = sk;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-      for (int k = 0; k < NB; ++k) sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+      for (int k = 0; k < NB; ++k)
+        if (k < nb) sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       const int sl = sb + k;
@@ -710,7 +729,7 @@ template <typename GRP>
 __device__ __forceinline__ GRP make_group(const KArgs &A);
 template <>
 __device__ __forceinline__ GridGrp make_group<GridGrp>(const KArgs &A) {
-  return GridGrp{&A.ctl->bar, &A.ctl->status, 0ull, A.u};
+  return GridGrp{&A.ctl->bar, &A.ctl->status, 0ull, A.u, A.timeout_ns, A.stall_barrier};
 }
 template <>
 __device__ __forceinline__ ClusterGrp make_group<ClusterGrp>(const KArgs &A) {
@@ -1669,7 +1688,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   ctx->stats.basis_passes += h->basis;
   ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
-    ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out";
+    ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
     return LPK_TIMEOUT;
   }
   return LPK_OK;
@@ -1745,6 +1764,8 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.u = W.u; A.z = W.z;
   A.part = ctx->kpart;
   A.ctl = (KrylovCtl *)ctx->kctl;
+  A.timeout_ns = ctx->wait_limit_ns;
+  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
   return A;
 }
 
@@ -1890,6 +1911,8 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   A.u = W.u; A.z = W.z;
   A.part = part;
   A.ctl = ctl;
+  A.timeout_ns = ctx->wait_limit_ns;
+  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
   A.f = f_hat;
   A.tol = tol;
   A.maxit = maxit;

@@ -99,6 +99,8 @@ struct lpk_ctx {
   int last_cluster = 0;          // cluster size of the last launch (0: grid)
   int resident_mode = 0;         // 0: rows cached in shared memory when they fit, 1: never
   int last_resident = 0;         // the last launch cached the rows
+  unsigned long long wait_limit_ns = 5000000000ull;  // bound of every grid-barrier wait
+  long long stall_barrier = 0;   // testing: grid barrier CTA 0 does not arrive at (0: none)
 
   // problems prepared on this context (freed with it)
   std::vector<lpk_problem *> problems;

@@ -27,7 +27,7 @@ NE_SSOR, NE_SOR = 0, 1
 
 # every symbol include/lpk.h declares
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
-           "lpk_reset_stats", "lpk_set_exec", "lpk_prepare",
+           "lpk_reset_stats", "lpk_set_exec", "lpk_set_wait_limit", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
            "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_ls_solve", "lpk_lp_solve",
            "lpk_lp_solve_batch", "lpk_server_default_config", "lpk_server_create", "lpk_server_destroy",
@@ -133,6 +133,7 @@ def load():
         "lpk_get_stats": (I32, [P, C.POINTER(Stats)]),
         "lpk_reset_stats": (I32, [P]),
         "lpk_set_exec": (I32, [P, I32, I32]),
+        "lpk_set_wait_limit": (I32, [P, D, I64]),
         "lpk_prepare": (I32, [P, C.POINTER(Matrix), C.c_uint64, C.POINTER(P)]),
         "lpk_problem_free": (None, [P]),
         "lpk_problem_dims": (I32, [P, P, P, P, P]),
@@ -244,6 +245,11 @@ class Context:
 
     def reset_stats(self):
         load().lpk_reset_stats(self._h)
+
+    def set_wait_limit(self, seconds=5.0, test_stall_barrier=0):
+        """Bound of every grid-barrier wait; test_stall_barrier (testing only)
+        makes every wait on that grid barrier run out (lpk_set_wait_limit)."""
+        _check(self._h, load().lpk_set_wait_limit(self._h, float(seconds), int(test_stall_barrier)))
 
     def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
         """Krylov kernel path: EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER or EXEC_BATCH

@@ -61,3 +61,49 @@ def test_reference_arm_prints_the_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "LPs/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_large_byte_formulas():
+    # one NE-SOR pass over FP32 values (half of the FP32 NE-SSOR sweep formula)
+    # and the FP64 product y = A x
+    assert bench.sweep_pass_bytes(1000, 10) == 1000 * 16 + 10 * 20
+    assert bench.sweep_pass_bytes_moved(1000, 10) == 1000 * 24 + 10 * 20
+    assert bench.spmv_bytes(1000, 10, 30) == 1000 * 12 + 10 * 16 + 30 * 8
+    # the large LP: about 44 MB per NE-SOR pass, about 34 MB per product
+    lp = gen.large_lp(1.0)
+    assert 40e6 < bench.sweep_pass_bytes(lp.nnz, lp.m) < 48e6
+    assert 30e6 < bench.spmv_bytes(lp.nnz, lp.m, lp.n) < 38e6
+
+
+def test_traffic_record_requires_unchanged_sources(tmp_path, monkeypatch):
+    import json
+    import os
+    rec_dir = tmp_path / "profiles"
+    rec_dir.mkdir()
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    digest = bench.source_digest(["k.cu"])
+    (rec_dir / "ncu_traffic.json").write_text(json.dumps(
+        {"sweep": {"sources": ["k.cu"], "sources_sha256": digest, "dram_bytes_per_launch": 1.5e7,
+                   "command": "ncu ..."}}))
+    assert bench.measured_traffic("sweep")[0] == 1.5e7
+    assert bench.measured_traffic("other")[0] is None
+    src.write_text("kernel v2")          # the kernel changed since the capture
+    assert bench.measured_traffic("sweep")[0] is None
+    assert os.path.exists(rec_dir / "ncu_traffic.json")
+
+
+def test_reference_arm_large_prints_the_contract_line():
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
+    assert line["config"]["workload"].startswith("large") and line["config"]["m"] == 150000
+    assert line["cpu_baseline"]["cores"] == 1
