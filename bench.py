@@ -449,6 +449,8 @@ def main():
                     help="serving: replay only the stream's LPs with m <= this (0: all)")
     ap.add_argument("--lp-steps", type=int, default=2,
                     help="large: timed steps of the assignment-LP solve throughput (0: skip)")
+    ap.add_argument("--x8", type=int, default=1,
+                    help="large: also time the sparse products on the matrix replicated 8x (0: skip)")
     ap.add_argument("--large-ipm", type=int, default=6,
                     help="large: interior-point iterations of the large LP run once (0: skip)")
     args = ap.parse_args()
@@ -536,9 +538,10 @@ def run_large(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
     st = ctx.stats()
     sweep_ms = st["krylov_ms"] / max(1, st["krylov_launches"])     # the sweep kernel alone (library events)
     sweep_ms = max_over_ranks(sweep_ms, dist, dev)
-    spmv_med = max_over_ranks(statistics.median(spmv_ms), dist, dev)
+    spmv_kernel_ms = max_over_ranks(st["spmv_ms"] / max(1, st["spmv_launches"]), dist, dev)
+    spmv_call_ms = max_over_ranks(statistics.median(spmv_ms), dist, dev)
     gbs = world * bsw / (sweep_ms / 1e3) / 1e9
-    gbs_spmv = world * bsp / (spmv_med / 1e3) / 1e9
+    gbs_spmv = world * bsp / (spmv_kernel_ms / 1e3) / 1e9
     hbm, src = peaks()
     traffic, traffic_src = measured_traffic("sweep_large_mixed")
     launches = st["launches"]
@@ -559,6 +562,36 @@ def run_large(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
            "d2h_bytes_per_step": int(out_z.nbytes + out_u.nbytes + out_y.nbytes),
            "what": "lpk_sweep + lpk_spmv on host arrays: host-to-device copies of d2, g, x and device-to-host "
                    "copies of z, u, y inside the timing; value = the sweep's algorithmic bytes / wall time"}
+
+    # sparse products on the large matrix replicated 8x on the block diagonal
+    # (170 MB of FP64 values and indices: larger than L2)
+    spmv_x8 = None
+    if args.x8:
+        m8, n8, rp8, ci8, val8 = replicated_csr(lp, 8)
+        P8 = lpk.Problem(ctx, m8, n8, torch.from_numpy(rp8).to(dev), torch.from_numpy(ci8).to(dev),
+                         torch.from_numpy(val8).to(dev))
+        gx = np.random.default_rng(7)
+        x8 = torch.from_numpy(gx.standard_normal(n8)).to(dev)
+        y8 = torch.from_numpy(gx.standard_normal(m8)).to(dev)
+        res = {}
+        for name, vec, tr in (("csr", x8, False), ("csc", y8, True)):
+            for _ in range(2):
+                P8.spmv(vec, transpose=tr)
+            ctx.reset_stats()
+            for _ in range(args.steps):
+                flush.zero_()
+                barrier()
+                P8.spmv(vec, transpose=tr)
+            st8 = ctx.stats()
+            ms8 = max_over_ranks(st8["spmv_ms"] / st8["spmv_launches"], dist, dev)
+            b8 = spmv_bytes(int(rp8[-1]), m8, n8) if not tr else spmv_bytes(int(rp8[-1]), n8, m8)
+            res[name] = {"ms": ms8, "bytes": b8, "gbs": world * b8 / (ms8 / 1e3) / 1e9,
+                         "frac": b8 / (ms8 / 1e3) / 1e9 / hbm}
+        res.update({"m": m8, "n": n8, "nnz": int(rp8[-1]),
+                    "what": "FP64 products A x (CSR) and A^T y (CSC) on the large matrix replicated 8x, kernel "
+                            "time by CUDA events, L2 flushed before each"})
+        spmv_x8 = res
+        P8.free()
 
     # the large LP's first interior-point iterations (the method stalls later on this family)
     large_solve = None
@@ -608,8 +641,11 @@ def run_large(args, wl, opts, lpk, torch, dev, local, rank, world, barrier, dist
         "sweep": {"ms": sweep_ms, "bytes": bsw, "bytes_moved_fp64_u": sweep_pass_bytes_moved(lp.nnz, lp.m),
                   "gbs": gbs, "frac": gbs / hbm / world, "colors": P.n_colors,
                   "us_per_color_phase": 1e3 * sweep_ms / max(1, P.n_colors)},
-        "spmv": {"ms": spmv_med, "bytes": bsp, "gbs": gbs_spmv, "frac": gbs_spmv / hbm / world,
-                 "what": "lpk_spmv y = A x in FP64 incl. the gather/scatter between input and internal numbering"},
+        "spmv": {"ms": spmv_kernel_ms, "bytes": bsp, "gbs": gbs_spmv, "frac": gbs_spmv / hbm / world,
+                 "call_ms": spmv_call_ms,
+                 "what": "y = A x in FP64: the product kernel's CUDA-event time inside lpk_spmv (call_ms: the whole "
+                         "call on the stream, with the gather/scatter between numberings and launch gaps)"},
+        "spmv_x8": spmv_x8,
         "roofline": {"bound": "hbm", "achieved": gbs / world, "peak": hbm, "unit": "GB/s", "frac": gbs / world / hbm,
                      "traffic": traffic, "traffic_source": traffic_src,
                      "kernel": "k_krylov<M_SWEEP, float, GridGrp> (one NE-SOR pass, grid path, rows cached in "

@@ -159,6 +159,10 @@ typedef struct lpk_stats {
   int64_t basis_passes;       /* AB-GMRES: m-row passes over one basis vector
                                  (four per vector and iteration in the two
                                  Gram-Schmidt passes, one per vector in V p) */
+  int64_t spmv_launches;      /* sparse-product kernels launched by lpk_spmv */
+  double spmv_ms;             /* their CUDA-event time on the context stream
+                                 (the product kernel alone, without the
+                                 gather/scatter between numberings) */
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.

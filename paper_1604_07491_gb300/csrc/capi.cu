@@ -312,18 +312,31 @@ LPK_API lpk_status lpk_spmv(lpk_ctx *ctx, lpk_problem *P, int32_t transpose, con
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &a.p, d.m + d.n + 2));
   b.p = nullptr;
   double *tm = a.p, *tn = a.p + d.m + 1;
+  if (!ctx->ev0) {
+    LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
+    LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
+  }
+  // the product kernel is timed alone (events on the context stream)
   if (transpose) {
     gather_m(ctx, d, vx.dev, tm);
+    LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     spmv_csc(ctx, d, tm, tn);
+    LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     scatter_n(ctx, d, tn, vy.dev, nullptr);
   } else {
     gather_n(ctx, d, vx.dev, tn);
+    LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     spmv_csr(ctx, d, tn, tm, nullptr, 1.0);
+    LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     scatter_m(ctx, d, tm, vy.dev);
   }
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   TRY(vy.finish());
   LPK_CUDA_TRY(ctx, ctx_sync(ctx));
+  float ms = 0.f;
+  LPK_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  ctx->stats.spmv_launches++;
+  ctx->stats.spmv_ms += ms;
   return LPK_OK;
 }
 

@@ -9,49 +9,6 @@ constexpr int TPB = 256;
 inline int wblk(long long rows, int tpb = TPB) { return (int)((rows * 32 + tpb - 1) / tpb); }
 inline int tblk(long long n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
-// ---- Sec. 3.5 row scaling --------------------------------------------------
-// d_j = sqrt(d2_j), rho_i = ||(A D)_i||_2, ahat = a_ij d_j / rho_i (FP64 and FP32)
-__global__ void k_scale(int m, const int *__restrict__ rp, const int *__restrict__ ci,
-                        const double *__restrict__ a, const double *__restrict__ d2,
-                        double *__restrict__ ah64, float *__restrict__ ah32, double *__restrict__ rho) {
-  const int lane = threadIdx.x & 31;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (r >= m) return;
-  const int k0 = rp[r], k1 = rp[r + 1];
-  double s = 0.0;
-  for (int k = k0 + lane; k < k1; k += 32) {
-    double e = a[k] * sqrt(d2[ci[k]]);
-    s += e * e;
-  }
-  s = warp_sum(s);
-  const double nr = sqrt(s);
-  for (int k = k0 + lane; k < k1; k += 32) {
-    double e = a[k] * sqrt(d2[ci[k]]);
-    double v = nr > 0.0 ? e / nr : 0.0;
-    ah64[k] = v;
-    ah32[k] = (float)v;
-  }
-  if (lane == 0) rho[r] = nr;
-}
-
-// the same scaled entries in CSC order: identical expression, so bitwise equal
-__global__ void k_scale_csc(int n, const int *__restrict__ cp, const int *__restrict__ ri,
-                            const double *__restrict__ at, const double *__restrict__ d2,
-                            const double *__restrict__ rho, double *__restrict__ aht) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double dj = sqrt(d2[j]);
-  for (int q = cp[j]; q < cp[j + 1]; ++q) {
-    const double e = at[q] * dj;
-    const double nr = rho[ri[q]];
-    aht[q] = nr > 0.0 ? e / nr : 0.0;
-  }
-}
-
-// Sparse products with LPR lanes per row (or column): short rows leave most
-// of a warp idle with one row per warp, so a warp takes 32 / LPR rows at once
-// (more independent loads in flight per warp); the partial sums of a row are
-// combined by shuffles inside its LPR-lane group, in a fixed order.
 template <int LPR>
 __device__ __forceinline__ double group_sum(double v) {
 #pragma unroll
@@ -59,38 +16,138 @@ __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
-// y = sign * A x + add
+// ---- Sec. 3.5 row scaling --------------------------------------------------
+// d_j = sqrt(d2_j), rho_i = ||(A D)_i||_2, ahat = a_ij d_j / rho_i (FP64 and FP32).
+// Square roots and divisions are multi-instruction FP64 sequences, and FP64
+// is scarce on this GPU: d is taken once per column (k_sqrt), 1 / rho once per
+// row, and every entry is (a_ij d_j) * (1 / rho_i) -- within an ulp or two of
+// the quotient.
+__global__ void k_sqrt(int n, const double *__restrict__ d2, double *__restrict__ d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) d[j] = sqrt(d2[j]);
+}
+
+template <int LPR>
+__global__ void k_scale(int m, const int *__restrict__ rp, const int *__restrict__ ci,
+                        const double *__restrict__ a, const double *__restrict__ d,
+                        double *__restrict__ ah64, float *__restrict__ ah32, double *__restrict__ rho,
+                        double *__restrict__ rinv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = (int)(t / LPR), sub = (int)(t % LPR);
+  int k0 = 0, k1 = 0;
+  double s = 0.0;
+  if (r < m) {
+    k0 = __ldg(rp + r);
+    k1 = __ldg(rp + r + 1);
+    for (int k = k0 + sub; k < k1; k += LPR) {
+      const double e = __ldg(a + k) * __ldg(d + __ldg(ci + k));
+      s += e * e;
+    }
+  }
+  s = group_sum<LPR>(s);  // every lane of the warp takes part
+  if (r >= m) return;
+  const double nr = sqrt(s);
+  const double ri = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (int k = k0 + sub; k < k1; k += LPR) {
+    const double v = (__ldg(a + k) * __ldg(d + __ldg(ci + k))) * ri;
+    ah64[k] = v;
+    ah32[k] = (float)v;
+  }
+  if (sub == 0) {
+    rho[r] = nr;
+    rinv[r] = ri;
+  }
+}
+
+// the same scaled entries in CSC order: identical expression, so bitwise equal
+__global__ void k_scale_csc(int n, const int *__restrict__ cp, const int *__restrict__ ri,
+                            const double *__restrict__ at, const double *__restrict__ d,
+                            const double *__restrict__ rinv, double *__restrict__ aht) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double dj = d[j];
+  for (int q = cp[j]; q < cp[j + 1]; ++q) aht[q] = (__ldg(at + q) * dj) * __ldg(rinv + __ldg(ri + q));
+}
+
+// Sparse products with LPR lanes per row (or column): short rows leave most
+// of a warp idle with one row per warp, so a warp takes 32 / LPR rows at once
+// (more independent loads in flight per warp); the partial sums of a row are
+// combined by shuffles inside its LPR-lane group, in a fixed order.
+
+// y = sign * A x + add.  A group of LPR lanes per row; each lane walks the
+// row's entries lane, lane + LPR, ... four at a time: the four (index, value)
+// loads and then the four gathers of x are issued before the first
+// multiply-add, so a lane has several independent loads in flight instead of
+// one dependent chain per entry.  The multiply-adds stay in entry order, so
+// the sums are those of the one-entry-at-a-time loop.
 template <int LPR>
 __global__ void k_spmv_csr(int m, const int *__restrict__ rp, const int *__restrict__ ci,
                            const double *__restrict__ a, const double *__restrict__ x,
                            double *__restrict__ y, const double *__restrict__ add, double sign) {
+  constexpr int U = 4;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = (int)(t / LPR), sub = (int)(t % LPR);
   double s = 0.0;
-  if (r < m)
-    for (int k = __ldg(rp + r) + sub, k1 = __ldg(rp + r + 1); k < k1; k += LPR) s += __ldg(a + k) * __ldg(x + __ldg(ci + k));
+  if (r < m) {
+    const int k1 = __ldg(rp + r + 1);
+    for (int k = __ldg(rp + r) + sub; k < k1; k += U * LPR) {
+      int c[U];
+      double av[U], xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kk = k + u * LPR;
+        c[u] = kk < k1 ? __ldg(ci + kk) : 0;
+        av[u] = kk < k1 ? __ldcs(a + kk) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = k + u * LPR < k1 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k + u * LPR < k1) s += av[u] * xv[u];
+    }
+  }
   s = group_sum<LPR>(s);  // every lane of the warp takes part
-  if (r < m && sub == 0) y[r] = sign * s + (add ? add[r] : 0.0);
+  if (r < m && sub == 0) y[r] = add ? sign * s + add[r] : (sign == 1.0 ? s : sign * s);
 }
 
-// y = A^T x through the CSC
+// y = A^T x through the CSC, organised as k_spmv_csr
 template <int LPR>
 __global__ void k_spmv_csc(int n, const int *__restrict__ cp, const int *__restrict__ ri,
                            const double *__restrict__ at, const double *__restrict__ x,
                            double *__restrict__ y) {
+  constexpr int U = 4;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int j = (int)(t / LPR), sub = (int)(t % LPR);
   double s = 0.0;
-  if (j < n)
-    for (int q = __ldg(cp + j) + sub, q1 = __ldg(cp + j + 1); q < q1; q += LPR) s += __ldg(at + q) * __ldg(x + __ldg(ri + q));
+  if (j < n) {
+    const int q1 = __ldg(cp + j + 1);
+    for (int q = __ldg(cp + j) + sub; q < q1; q += U * LPR) {
+      int c[U];
+      double av[U], xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int qq = q + u * LPR;
+        c[u] = qq < q1 ? __ldg(ri + qq) : 0;
+        av[u] = qq < q1 ? __ldcs(at + qq) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = q + u * LPR < q1 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q + u * LPR < q1) s += av[u] * xv[u];
+    }
+  }
   s = group_sum<LPR>(s);
   if (j < n && sub == 0) y[j] = s;
 }
 
-// lanes per row from the mean row length
+// Lanes per row from the mean row length.  Each level of the group's shuffle
+// reduction is one FP64 add per row, and an FP64 warp instruction occupies a
+// sub-partition's FP64 pipe for tens of cycles on this GPU, so the group is
+// kept narrow (about four entries per lane) rather than one entry per lane.
 inline int lanes_for(long long nnz, long long rows) {
   const long long avg = rows > 0 ? (nnz + rows - 1) / rows : 0;
-  return avg <= 8 ? 4 : avg <= 24 ? 8 : avg <= 64 ? 16 : 32;
+  return avg <= 8 ? 2 : avg <= 32 ? 4 : avg <= 64 ? 8 : avg <= 128 ? 16 : 32;
 }
 inline int gblk(long long rows, int lpr, int tpb = TPB) { return (int)((rows * lpr + tpb - 1) / tpb); }
 
@@ -118,13 +175,24 @@ __global__ void k_fill(int len, double v, double *__restrict__ out) {
 
 // ---------------------------------------------------------------------------
 void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2) {
-  if (P.m > 0) LPK_LAUNCH(ctx, k_scale, wblk(P.m), TPB, 0, ctx->stream, P.m, P.rp, P.ci, P.a, d2, P.ah64, P.ah32, P.rho);
-  if (P.n > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.n), TPB, 0, ctx->stream, P.n, P.cp, P.ri, P.at, d2, P.rho, P.aht);
+  cudaStream_t s = ctx->stream;
+  if (P.n > 0) LPK_LAUNCH(ctx, k_sqrt, tblk(P.n), TPB, 0, s, P.n, d2, P.dcol);
+  if (P.m > 0) {
+    switch (lanes_for(P.nnz, P.m)) {
+      case 2: LPK_LAUNCH(ctx, k_scale<2>, gblk(P.m, 2), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+      case 4: LPK_LAUNCH(ctx, k_scale<4>, gblk(P.m, 4), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+      case 8: LPK_LAUNCH(ctx, k_scale<8>, gblk(P.m, 8), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+      case 16: LPK_LAUNCH(ctx, k_scale<16>, gblk(P.m, 16), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+      default: LPK_LAUNCH(ctx, k_scale<32>, gblk(P.m, 32), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+    }
+  }
+  if (P.n > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.n), TPB, 0, s, P.n, P.cp, P.ri, P.at, P.dcol, P.rinv, P.aht);
 }
 void spmv_csr(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y, const double *add, double sign) {
   if (P.m <= 0) return;
   cudaStream_t s = ctx->stream;
   switch (lanes_for(P.nnz, P.m)) {
+    case 2: LPK_LAUNCH(ctx, k_spmv_csr<2>, gblk(P.m, 2), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
     case 4: LPK_LAUNCH(ctx, k_spmv_csr<4>, gblk(P.m, 4), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
     case 8: LPK_LAUNCH(ctx, k_spmv_csr<8>, gblk(P.m, 8), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
     case 16: LPK_LAUNCH(ctx, k_spmv_csr<16>, gblk(P.m, 16), TPB, 0, s, P.m, P.rp, P.ci, P.a, x, y, add, sign); break;
@@ -135,6 +203,7 @@ void spmv_csc(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y) {
   if (P.n <= 0) return;
   cudaStream_t s = ctx->stream;
   switch (lanes_for(P.nnz, P.n)) {
+    case 2: LPK_LAUNCH(ctx, k_spmv_csc<2>, gblk(P.n, 2), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
     case 4: LPK_LAUNCH(ctx, k_spmv_csc<4>, gblk(P.n, 4), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
     case 8: LPK_LAUNCH(ctx, k_spmv_csc<8>, gblk(P.n, 8), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;
     case 16: LPK_LAUNCH(ctx, k_spmv_csc<16>, gblk(P.n, 16), TPB, 0, s, P.n, P.cp, P.ri, P.at, x, y); break;

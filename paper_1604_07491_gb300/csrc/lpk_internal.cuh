@@ -40,6 +40,8 @@ struct DevProblem {
   double *ah64 = nullptr;        // [nnz] A_hat = D_cal^-1 A D, FP64
   float *ah32 = nullptr;         // [nnz] A_hat, FP32 copy for the mixed inner sweeps
   double *rho = nullptr;         // [m]   row norms of A D
+  double *rinv = nullptr;        // [m]   1 / rho (0 for empty rows)
+  double *dcol = nullptr;        // [n]   d = sqrt(d2) of the last scaling
 
   // CSC of the permuted matrix (row indices are sweep positions, sorted)
   int *cp = nullptr;             // [n+1]

@@ -299,7 +299,7 @@ void free_problem(DevProblem &P) {
   void *ptrs[] = {P.pos_of_in_row, P.in_row_of_pos, P.col_of_in, P.in_col_of, P.color_in, P.rp,
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
-                  P.gm_V,          P.ipm_buf};
+                  P.gm_V,          P.ipm_buf,       P.rinv,      P.dcol};
   for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }
@@ -476,6 +476,8 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah64, nnz));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah32, nnz));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rho, mr));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rinv, mr));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.dcol, nr));
   if (mr > 0) LPK_LAUNCH(ctx, k_perm_rowlen, nblk(mr), TPB, 0, st, mr, perm, rp_red, rlen);
   LPK_LAUNCH(ctx, k_scan<int>, 1, 1024, 0, st, mr, rlen, P.rp);
   if (mr > 0)

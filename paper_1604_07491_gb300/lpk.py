@@ -80,7 +80,8 @@ class Stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("krylov_launches", C.c_int64), ("krylov_ms", C.c_double),
                 ("krylov_iters", C.c_int64), ("sweep_passes", C.c_int64), ("row_passes", C.c_int64),
                 ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
-                ("last_resident", C.c_int32), ("basis_passes", C.c_int64)]
+                ("last_resident", C.c_int32), ("basis_passes", C.c_int64), ("spmv_launches", C.c_int64),
+                ("spmv_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
