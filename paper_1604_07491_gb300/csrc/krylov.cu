@@ -43,6 +43,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "lpk_internal.cuh"
@@ -126,6 +127,71 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   return v;
 }
 
+// ---- double-word (FP32 pair) arithmetic of the mixed-precision sweeps ------
+// A value is the unevaluated sum hi + lo of two floats.  FP64 instructions
+// occupy an SM sub-partition's FP64 pipe for tens of cycles each on this GPU
+// (about 1.2 TFLOP/s for the whole chip, against about 70 for FP32), so the
+// sweeps over the FP32 copy of the scaled matrix keep u and z as double
+// words and run every operation of a row on the FP32 pipes.  The building
+// blocks are the classical error-free transformations -- Knuth's TwoSum,
+// Dekker's Fast2Sum (|a| >= |b|), the FMA-based exact product -- and the
+// double-word addition of Joldes, Muller and Popescu (ACM TOMS 44(2), 2017:
+// "AccurateDWPlusDW", relative error <= 3u^2 + 13u^3 with u = 2^-24) and their
+// double-word times float product (relative error <= 2u^2).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ float2 dw_add(float2 x, float2 y) {
+  float sh, sl, th, tl;
+  two_sum(x.x, y.x, sh, sl);
+  two_sum(x.y, y.y, th, tl);
+  sl += th;
+  fast_two_sum(sh, sl, sh, sl);
+  sl += tl;
+  float zh, zl;
+  fast_two_sum(sh, sl, zh, zl);
+  return make_float2(zh, zl);
+}
+__device__ __forceinline__ float2 dw_mulf(float2 x, float a) {
+  const float p = x.x * a;
+  float e = fmaf(x.x, a, -p);
+  e = fmaf(x.y, a, e);
+  float zh, zl;
+  fast_two_sum(p, e, zh, zl);
+  return make_float2(zh, zl);
+}
+__device__ __forceinline__ float2 dw_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  float e = fmaf(x.x, y.x, -p);
+  e = fmaf(x.x, y.y, e);
+  e = fmaf(x.y, y.x, e);
+  float zh, zl;
+  fast_two_sum(p, e, zh, zl);
+  return make_float2(zh, zl);
+}
+__device__ __forceinline__ float2 dw_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 dw_of(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ double dw_val(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ float2 shfl_xor_dw(float2 v, int o) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+template <typename T>
+__device__ __forceinline__ float2 as_dw(const T &bits) {
+  static_assert(sizeof(T) == 8, "double-word slots are 8 bytes");
+  float2 v;
+  memcpy(&v, &bits, 8);
+  return v;
+}
+
 // work counters (every thread keeps identical copies; CTA 0 reports them)
 struct Counters {
   long long passes = 0, rows = 0, cols = 0, basis = 0;
@@ -178,6 +244,9 @@ struct GridGrp {
   __device__ __forceinline__ long long barriers() const { return (long long)epoch; }
   __device__ __forceinline__ double uld(int j) const { return __ldcg(u + j); }
   __device__ __forceinline__ void ust(int j, double v) const { u[j] = v; }
+  // double-word view of the same 8-byte slots (mixed-precision sweeps)
+  __device__ __forceinline__ float2 uld2(int j) const { return __ldcg(reinterpret_cast<const float2 *>(u) + j); }
+  __device__ __forceinline__ void ust2(int j, float2 v) const { reinterpret_cast<float2 *>(u)[j] = v; }
   __device__ __forceinline__ void uzero(int n) const {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) u[j] = 0.0;
   }
@@ -202,6 +271,11 @@ struct ClusterGrp {
   }
   __device__ __forceinline__ double uld(int j) const { return *(volatile double *)up(j); }
   __device__ __forceinline__ void ust(int j, double v) const { *up(j) = v; }
+  __device__ __forceinline__ float2 uld2(int j) const {
+    const unsigned long long b = *(volatile unsigned long long *)up(j);
+    return as_dw(b);
+  }
+  __device__ __forceinline__ void ust2(int j, float2 v) const { *reinterpret_cast<float2 *>(up(j)) = v; }
   __device__ __forceinline__ void uzero(int) const {
     for (unsigned i = threadIdx.x; i <= mask; i += blockDim.x) u_sm[i] = 0.0;
   }
@@ -515,6 +589,151 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
   }
 }
 
+// ---- double-word row updates (FP32 values, u and z as double words) -------
+// The same row arithmetic as row_update / row_update_res / rows_res_short --
+// d = omega (g_r - (a_r, u)), u += d a_r -- with every product, sum and
+// update in double-word FP32 (see dw_add); d is returned as a double word.
+
+// one row from registers (rows streamed from global memory)
+template <typename GRP>
+__device__ __forceinline__ float2 row_update_dw(const GRP &Gp, const KArgs &A, const float *__restrict__ a,
+                                                const RowPre<float> &P, float2 g2, float2 om2, bool om1) {
+  const int lane = threadIdx.x & 31;
+  float2 s = make_float2(0.f, 0.f);
+  if (P.len <= 32 * RC) {
+    float2 uv[RC];
+#pragma unroll
+    for (int e = 0; e < RC; ++e)
+      if (lane + 32 * e < P.len) {
+        uv[e] = Gp.uld2(P.cv[e]);
+        s = dw_add(s, dw_mulf(uv[e], P.av[e]));
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = dw_add(s, shfl_xor_dw(s, o));
+    float2 d = dw_add(g2, dw_neg(s));
+    if (!om1) d = dw_mul(d, om2);
+#pragma unroll
+    for (int e = 0; e < RC; ++e)
+      if (lane + 32 * e < P.len) Gp.ust2(P.cv[e], dw_add(uv[e], dw_mulf(d, P.av[e])));
+    return d;
+  }
+  const int k1 = P.k0 + P.len;
+  for (int k = P.k0 + lane; k < k1; k += 32) s = dw_add(s, dw_mulf(Gp.uld2(__ldg(A.ci + k)), __ldg(a + k)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = dw_add(s, shfl_xor_dw(s, o));
+  float2 d = dw_add(g2, dw_neg(s));
+  if (!om1) d = dw_mul(d, om2);
+  for (int k = P.k0 + lane; k < k1; k += 32) {
+    const int c = __ldg(A.ci + k);
+    Gp.ust2(c, dw_add(Gp.uld2(c), dw_mulf(d, __ldg(a + k))));
+  }
+  return d;
+}
+
+// one row from the shared-memory row cache
+template <typename GRP>
+__device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *vals, const int *cols, int e0,
+                                                    int len, float2 g2, float2 om2, bool om1) {
+  const int lane = threadIdx.x & 31;
+  float2 s = make_float2(0.f, 0.f);
+  if (len <= 32 * RCR) {
+    int cv[RCR];
+    float av[RCR];
+    float2 uv[RCR];
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) {
+        cv[e] = cols[e0 + lane + 32 * e];
+        av[e] = vals[e0 + lane + 32 * e];
+      }
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) uv[e] = Gp.uld2(cv[e]);
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) s = dw_add(s, dw_mulf(uv[e], av[e]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = dw_add(s, shfl_xor_dw(s, o));
+    float2 d = dw_add(g2, dw_neg(s));
+    if (!om1) d = dw_mul(d, om2);
+#pragma unroll
+    for (int e = 0; e < RCR; ++e)
+      if (lane + 32 * e < len) Gp.ust2(cv[e], dw_add(uv[e], dw_mulf(d, av[e])));
+    return d;
+  }
+  for (int t = lane; t < len; t += 32) s = dw_add(s, dw_mulf(Gp.uld2(cols[e0 + t]), vals[e0 + t]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = dw_add(s, shfl_xor_dw(s, o));
+  float2 d = dw_add(g2, dw_neg(s));
+  if (!om1) d = dw_mul(d, om2);
+  for (int t = lane; t < len; t += 32) {
+    const int c = cols[e0 + t];
+    Gp.ust2(c, dw_add(Gp.uld2(c), dw_mulf(d, vals[e0 + t])));
+  }
+  return d;
+}
+
+// up to four short rows (at most 64 entries) of one color from the row cache,
+// gathers first and the reductions interleaved, as rows_res_short
+template <typename GRP>
+__device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *vals, const int *cols,
+                                                  const int2 *dw, const float2 *gs2, float2 *zw2, int s0, int s1,
+                                                  float2 om2, bool om1, bool firstpass) {
+  constexpr int NB = 4, E = 2;
+  const int lane = threadIdx.x & 31;
+  for (int sb = s0; sb < s1; sb += NB) {
+    const int nb = min(NB, s1 - sb);
+    int cv[NB][E];
+    float av[NB][E];
+    float2 uv[NB][E], sm[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const int2 kl = sb + k < s1 ? dw[sb + k] : make_int2(0, 0);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int t = lane + 32 * e;
+        cv[k][e] = -1;
+        av[k][e] = 0.f;
+        if (t < kl.y) {
+          cv[k][e] = cols[kl.x + t];
+          av[k][e] = vals[kl.x + t];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+#pragma unroll
+      for (int e = 0; e < E; ++e) uv[k][e] = cv[k][e] >= 0 ? Gp.uld2(cv[k][e]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      float2 sk = make_float2(0.f, 0.f);
+      if (k < nb) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) sk = dw_add(sk, dw_mulf(uv[k][e], av[k][e]));
+      }
+      sm[k] = sk;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (k < nb) sm[k] = dw_add(sm[k], shfl_xor_dw(sm[k], o));
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      const int sl = sb + k;
+      if (k < nb) {
+        float2 d = dw_add(gs2[sl], dw_neg(sm[k]));
+        if (!om1) d = dw_mul(d, om2);
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) Gp.ust2(cv[k][e], dw_add(uv[k][e], dw_mulf(d, av[k][e])));
+        if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
+      }
+    }
+  }
+}
+
 // inner_sweeps with every row of the warp resident in shared memory: the only
 // global/distributed accesses of a color phase are the gather and scatter of u.
 template <typename TV, typename GRP>
@@ -530,6 +749,45 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
   const TV *vals = (const TV *)Z.vals;
   const int *cols = Z.cols;
   const int nslots = cw[nc];
+  if constexpr (std::is_same<TV, float>::value) {
+    // FP32 values: double-word rows; z and g slots hold double words, and the
+    // (z, g) product of the last pass is formed when z is written out
+    float2 *zw2 = reinterpret_cast<float2 *>(zw), *gs2 = reinterpret_cast<float2 *>(gsw);
+    for (int sl = lane; sl < nslots; sl += 32) gs2[sl] = dw_of(ldcg(g + rsw[sl]));  // g once per sweep
+    __syncwarp();
+    const float2 om2 = dw_of(om);
+    const bool om1 = om == 1.0;
+    C.passes += passes;
+    for (int ps = 0; ps < passes; ++ps) {
+      const bool backward = ssor && (ps & 1);
+      const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+      for (int cc = 0; cc < nc; ++cc) {
+        const int c = backward ? nc - 1 - cc : cc;
+        if (A.short_rows) {
+          rows_res_short_dw(Gp, vals, cols, dw, gs2, zw2, cw[c], cw[c + 1], om2, om1, firstpass);
+        } else {
+          for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
+            const int2 kl = dw[sl];
+            const float2 d = row_update_res_dw(Gp, vals, cols, kl.x, kl.y, gs2[sl], om2, om1);
+            if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
+          }
+        }
+        if (!(lastpass && cc == nc - 1)) {
+          if (!Gp.sync(s_ok)) return false;
+        }
+      }
+    }
+    __syncwarp();
+    for (int sl = lane; sl < nslots; sl += 32) {
+      const double zr = dw_val(zw2[sl]);
+      A.z[rsw[sl]] = zr;
+      if (acc) *acc += zr * ldcg(g + rsw[sl]);
+    }
+    if (!acc) {
+      if (!Gp.sync(s_ok)) return false;
+    }
+    return true;
+  }
   for (int sl = lane; sl < nslots; sl += 32) gsw[sl] = ldcg(g + rsw[sl]);  // g once per sweep
   __syncwarp();
   C.passes += passes;
@@ -600,6 +858,43 @@ __device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g
     row_fetch<TV>(A, a, g, rsw[sl], dw[sl], cur);
   }
   int q = 0;
+  if constexpr (std::is_same<TV, float>::value) {
+    // FP32 values: double-word rows and z slots (see inner_sweeps_res)
+    float2 *zw2 = reinterpret_cast<float2 *>(zw);
+    const float2 om2 = dw_of(om);
+    const bool om1 = om == 1.0;
+    for (int ps = 0; ps < passes; ++ps) {
+      const bool backward = ssor && (ps & 1);
+      const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+      for (int cc = 0; cc < nc; ++cc) {
+        const int c = backward ? nc - 1 - cc : cc;
+        const int nrow = cw[c + 1] - cw[c];
+        for (int k = 0; k < nrow; ++k, ++q) {
+          const int sl = slot_of(q);
+          if (q + 1 < Q) {
+            const int s2 = slot_of(q + 1);
+            row_fetch<TV>(A, a, g, rsw[s2], dw[s2], nxt);
+          }
+          const float2 d = row_update_dw(Gp, A, a, cur, dw_of(cur.g), om2, om1);
+          if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
+          if (q + 1 < Q) cur = nxt;
+        }
+        if (!(lastpass && cc == nc - 1)) {
+          if (!Gp.sync(s_ok)) return false;
+        }
+      }
+    }
+    __syncwarp();
+    for (int sl = lane; sl < S; sl += 32) {
+      const double zr = dw_val(zw2[sl]);
+      A.z[rsw[sl]] = zr;
+      if (acc) *acc += zr * ldcg(g + rsw[sl]);
+    }
+    if (!acc) {
+      if (!Gp.sync(s_ok)) return false;
+    }
+    return true;
+  }
   for (int ps = 0; ps < passes; ++ps) {
     const bool backward = ssor && (ps & 1);
     const bool firstpass = ps == 0, lastpass = ps == passes - 1;
@@ -749,7 +1044,12 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
   Counters Cn;
   const ZStore Z = make_zstore(A);
   zstore_init<TV>(A, Z, Gp.rank() * KWPB + (threadIdx.x >> 5), Gp.size() * KWPB);
-  auto uget = [&](int j) { return Gp.uld(j); };
+  // u is read outside the sweeps only in FP64 runs and in the sweep-only mode;
+  // with FP32 values its slots hold double words
+  auto uget = [&](int j) -> double {
+    if constexpr (std::is_same<TV, float>::value) return dw_val(Gp.uld2(j));
+    else return Gp.uld(j);
+  };
   auto zget = [&](int i) { return ldcg(A.z + i); };
 
   // ---- sweep-only mode (lpk_sweep) ----------------------------------------
