@@ -930,15 +930,34 @@ __device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g
 }
 
 // t = A_hat x in double (rows split over warps), x gathered as x(c) (a
-// callable); t = sub - A_hat x when sub is non-null
+// callable); t = sub - A_hat x when sub is non-null.  A lane takes its row
+// entries lane, lane + 32, ... four at a time: the four (index, value)
+// loads, then the four gathers of x, then the multiply-adds in entry order
+// (the sums of the one-entry-at-a-time loop), so a lane has several
+// independent L2 loads in flight instead of one dependent chain per entry.
 template <typename GRP, typename XF>
 __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, double *t, const double *sub) {
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
   const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
   for (int r = gw; r < A.m; r += GW) {
     const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
     double s = 0.0;
-    for (int k = k0 + lane; k < k1; k += 32) s += __ldg(A.a64 + k) * x(__ldg(A.ci + k));
+    for (int k = k0 + lane; k < k1; k += 32 * U) {
+      int c[U];
+      double av[U], xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kk = k + 32 * u;
+        c[u] = kk < k1 ? __ldg(A.ci + kk) : 0;
+        av[u] = kk < k1 ? __ldg(A.a64 + kk) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = k + 32 * u < k1 ? x(c[u]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (k + 32 * u < k1) s += av[u] * xv[u];
+    }
     s = warp_sum(s);
     if (lane == 0) t[r] = sub ? ldcg(sub + r) - s : s;
   }
@@ -968,12 +987,29 @@ __device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, co
       len = max(len, q1[u] - q0[u]);
       sv[u] = 0.0;
     }
-    for (int t = 0; t < len; ++t) {
+    // two entries of each of the CW columns per step: their row-index and
+    // value loads, then their gathers, then the multiply-adds in entry order
+    constexpr int TE = 2;
+    for (int t = 0; t < len; t += TE) {
+      int rr[CW][TE];
+      double av[CW][TE], xv[CW][TE];
 #pragma unroll
-      for (int u = 0; u < CW; ++u) {
-        const int q = q0[u] + t;
-        if (q < q1[u]) sv[u] += __ldg(A.aht + q) * ldcg(x + __ldg(A.ri + q));
-      }
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e) {
+          const int q = q0[u] + t + e;
+          rr[u][e] = q < q1[u] ? __ldg(A.ri + q) : 0;
+          av[u][e] = q < q1[u] ? __ldg(A.aht + q) : 0.0;
+        }
+#pragma unroll
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e) xv[u][e] = q0[u] + t + e < q1[u] ? ldcg(x + rr[u][e]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e)
+          if (q0[u] + t + e < q1[u]) sv[u] += av[u][e] * xv[u][e];
     }
 #pragma unroll
     for (int u = 0; u < CW; ++u) {
@@ -1275,9 +1311,23 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         for (int r = rlo + wi; r < rhi; r += KWPB) {
           const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
           double sacc = 0.0;
-          for (int q = k0 + lane; q < k1; q += 32) {
-            const int c = __ldg(A.ci + q);
-            sacc += __ldg(A.a64 + q) * (A.wy ? ldcg(uwv + c) : Gp.uld(c));
+          // four entries per lane at a time, loads before multiply-adds (as spmv_rows)
+          constexpr int U = 4;
+          for (int q = k0 + lane; q < k1; q += 32 * U) {
+            int c[U];
+            double av[U], xv[U];
+#pragma unroll
+            for (int e = 0; e < U; ++e) {
+              const int qq = q + 32 * e;
+              c[e] = qq < k1 ? __ldg(A.ci + qq) : 0;
+              av[e] = qq < k1 ? __ldg(A.a64 + qq) : 0.0;
+            }
+#pragma unroll
+            for (int e = 0; e < U; ++e)
+              xv[e] = q + 32 * e < k1 ? (A.wy ? ldcg(uwv + c[e]) : Gp.uld(c[e])) : 0.0;
+#pragma unroll
+            for (int e = 0; e < U; ++e)
+              if (q + 32 * e < k1) sacc += av[e] * xv[e];
           }
           sacc = warp_sum(sacc);
           if (lane == 0) {
@@ -1292,23 +1342,37 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           double *h = pass == 0 ? A.h1 : A.h2;
           // partial dots (w, v_i) over this CTA's rows: lanes over 32 basis
           // vectors (one coalesced 256-byte load of a row of V), warps over
-          // rows; the warps' partials are summed in warp order in shared memory
-          for (int i0 = 0; i0 <= kk; i0 += 32) {
-            const int i = i0 + lane;
-            double acc = 0.0;
-            if (i <= kk) {
-#pragma unroll 4
-              for (int r = rlo + wi; r < rhi; r += KWPB) acc += ldcg(A.wt + r) * ldcg(A.V + (size_t)r * ld + i);
-            }
-            s_dot[wi][lane] = acc;
-            __syncthreads();
-            if (wi == 0 && i <= kk) {
-              double t = 0.0;
+          // rows.  A warp walks its rows once per block of DC x 32 basis
+          // vectors, keeping the DC chunk sums in registers, so the loads of
+          // a row's DC chunks are in flight together; the warps' partials are
+          // then summed in warp order in shared memory, chunk by chunk (the
+          // same sums, in the same order, as one chunk at a time)
+          constexpr int DC = 4;
+          for (int ib = 0; ib <= kk; ib += 32 * DC) {
+            double acc[DC];
 #pragma unroll
-              for (int w = 0; w < KWPB; ++w) t += s_dot[w][lane];
-              A.gpart[(size_t)b * ld + i] = t;
+            for (int c = 0; c < DC; ++c) acc[c] = 0.0;
+            for (int r = rlo + wi; r < rhi; r += KWPB) {
+              const double wr = ldcg(A.wt + r);
+              const double *vr = A.V + (size_t)r * ld + ib + lane;
+#pragma unroll
+              for (int c = 0; c < DC; ++c)
+                if (ib + 32 * c + lane <= kk) acc[c] += wr * ldcg(vr + 32 * c);
             }
-            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < DC; ++c) {
+              const int i = ib + 32 * c + lane;
+              if (ib + 32 * c > kk) break;  // warp-uniform
+              s_dot[wi][lane] = acc[c];
+              __syncthreads();
+              if (wi == 0 && i <= kk) {
+                double t = 0.0;
+#pragma unroll
+                for (int w = 0; w < KWPB; ++w) t += s_dot[w][lane];
+                A.gpart[(size_t)b * ld + i] = t;
+              }
+              __syncthreads();
+            }
           }
           if (!Gp.sync(&s_ok)) return;
           // h_i = sum of the G partials in CTA order: a thread per i for a

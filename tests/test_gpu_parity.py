@@ -494,3 +494,33 @@ def test_large_first_ipm_iterations(lpk, ctx, precision):
             idx = np.array(G["indices"][name])
             assert ew(v[idx], np.array(ref["samples"][name])) < 1e-4, (k, name)
             assert abs(np.linalg.norm(v) - ref["norms"][name]) <= 1e-6 * ref["norms"][name], (k, name)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_large_family_full_solve_scale003(lpk, ctx, precision):
+    """The large power-law family at scale 0.03 (m = 4,500, n = 13,037) solved
+    completely with AB-GMRES (NE-SOR, ell = 1), against the oracle's complete
+    solve (tests/golden/large_s003_solve.json, written by
+    make_large_golden.py): objective within 1e-7, the certificates <= 1e-8
+    recomputed here from the returned vectors, and x, y, s element-wise within
+    1e-6 on the stored sample (the optimum is unique)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "large_s003_solve.json")
+    G = json.load(open(path))
+    lp = gen.large_lp(0.03)
+    assert (G["m"], G["n"], G["nnz"]) == (lp.m, lp.n, lp.nnz)
+    assert G["info"]["status_name"] == "OK"
+    opts = dict(G["options"])
+    opts["solver"] = opts.pop("method")
+    P = lpk.Problem.from_lp(ctx, lp, device="cuda")
+    x, y, s, info = P.lp_solve(lp.b, lp.c, precision=precision, **opts)
+    assert info["status_name"] == "OK", info
+    ref = G["info"]["obj_primal"]
+    assert abs(info["obj_primal"] - ref) <= 1e-7 * abs(ref)
+    pinf, dinf, gap = certs(lp, x, y, s)
+    assert pinf <= 1e-8 and dinf <= 1e-8 and gap <= 1e-8
+    for name, v in (("x", x), ("y", y), ("s", s)):
+        idx = np.array(G["indices"][name])
+        assert ew(v[idx], np.array(G["samples"][name])) < 1e-6, name
+    P.free()
