@@ -407,6 +407,8 @@ def sum_stats(ctxs):
         for k, v in c.stats().items():
             if k in ("last_cluster_size", "last_resident"):
                 tot.setdefault(k, []).append(v)
+            elif isinstance(v, list):
+                tot[k] = [a + b for a, b in zip(tot.get(k, [0.0] * len(v)), v)]
             else:
                 tot[k] = tot.get(k, 0) + v
     return tot

@@ -163,6 +163,13 @@ typedef struct lpk_stats {
   double spmv_ms;             /* their CUDA-event time on the context stream
                                  (the product kernel alone, without the
                                  gather/scatter between numberings) */
+  double phase_ms[4];         /* with phase timing on (lpk_set_phase_timing):
+                                 the persistent kernel's time between barriers,
+                                 by what the phase did: [0] vector updates,
+                                 reductions and the rest, [1] inner-sweep color
+                                 phases, [2] AB-GMRES/BA-GMRES orthogonalisation
+                                 (with the product w = A_hat z before it),
+                                 [3] the w-space image A_hat^T z */
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.
@@ -216,6 +223,12 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
  * is exercised without faulting the GPU.  The cluster path's hardware
  * barriers have no software wait and are not affected. */
 LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier);
+
+/* Phase timing of the persistent Krylov kernel (on != 0; default off): the
+ * first CTA reads %globaltimer at every barrier and charges the interval to
+ * the kind of phase that ended there (lpk_stats.phase_ms).  Costs one timer
+ * read and a shared-memory update per barrier in one thread. */
+LPK_API lpk_status lpk_set_phase_timing(lpk_ctx *ctx, int32_t on);
 
 /* Copy A to the device, validate it, remove empty rows and columns (the only
  * preprocessing of Sec. 4.2) and compute the multicolor row order on the

@@ -179,6 +179,12 @@ LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test
   return LPK_OK;
 }
 
+LPK_API lpk_status lpk_set_phase_timing(lpk_ctx *ctx, int32_t on) {
+  if (!ctx) return LPK_INVALID_ARG;
+  ctx->phase_timing = on ? 1 : 0;
+  return LPK_OK;
+}
+
 LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx) {
   if (!ctx) return LPK_INVALID_ARG;
   ctx->stats = lpk_stats{};

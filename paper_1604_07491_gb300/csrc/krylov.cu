@@ -69,6 +69,7 @@ struct KrylovCtl {
   double res0, res;
   long long passes, rows, cols, barriers;   // work counters of the launch
   long long basis;                          // AB-GMRES basis-vector passes
+  unsigned long long phase_ns[4];           // phase timing (KArgs.prof): other, sweep, Gram-Schmidt, products
 };
 
 struct KArgs {
@@ -93,6 +94,7 @@ struct KArgs {
   int gs_off, desc_off, val_off, rs_off, cum_off, col_off;
   int resident;                    // rows of each warp cached in shared memory
   int short_rows;                  // every row has at most 64 entries (batched row updates)
+  int prof;                        // phase timing: CTA 0 charges each barrier interval to its phase kind
   unsigned long long timeout_ns;   // grid path: bound of every barrier wait
   unsigned long long stall_barrier;  // grid path, testing: barrier CTA 0 does not arrive at (0: none)
   double *dw, *dy;                 // outputs (n), (m)
@@ -197,6 +199,24 @@ struct Counters {
   long long passes = 0, rows = 0, cols = 0, basis = 0;
 };
 
+// ---- phase timing ----------------------------------------------------------
+// With KArgs.prof, thread 0 of the group's first CTA reads %globaltimer at
+// every barrier exit and charges the interval since the previous one to the
+// current phase kind (0 other, 1 sweep color phases, 2 Gram-Schmidt, 3
+// products), so a launch's time splits by what its phases do.  The state
+// lives in shared memory: p[0] last time, p[1] kind, p[2 + k] nanoseconds.
+enum { PK_OTHER = 0, PK_SWEEP = 1, PK_GS = 2, PK_PROD = 3 };
+__device__ __forceinline__ void phase_tick(unsigned long long *p, bool first_cta) {
+  if (p && first_cta && threadIdx.x == 0) {
+    const unsigned long long now = globaltimer();
+    p[2 + p[1]] += now - p[0];
+    p[0] = now;
+  }
+}
+__device__ __forceinline__ void phase_kind(unsigned long long *p, int k) {
+  if (p && threadIdx.x == 0) p[1] = (unsigned long long)k;
+}
+
 // ---- group policies --------------------------------------------------------
 struct GridGrp {
   unsigned long long *cnt;
@@ -205,6 +225,7 @@ struct GridGrp {
   double *u;
   unsigned long long timeout_ns;  // bound of every wait
   unsigned long long stall;       // testing: CTA 0 does not arrive at this barrier (0: none)
+  unsigned long long *prof;       // phase timing in shared memory (null: off), see phase_tick
   __device__ __forceinline__ unsigned rank() const { return blockIdx.x; }
   __device__ __forceinline__ unsigned size() const { return gridDim.x; }
   // The CTA barrier orders this CTA's writes before thread 0's acq_rel add;
@@ -239,8 +260,10 @@ struct GridGrp {
       *s_ok = ok;
     }
     __syncthreads();
+    phase_tick(prof, blockIdx.x == 0);
     return *s_ok != 0;
   }
+  __device__ __forceinline__ void set_kind(int k) const { phase_kind(prof, k); }
   __device__ __forceinline__ long long barriers() const { return (long long)epoch; }
   __device__ __forceinline__ double uld(int j) const { return __ldcg(u + j); }
   __device__ __forceinline__ void ust(int j, double v) const { u[j] = v; }
@@ -256,6 +279,7 @@ struct ClusterGrp {
   double *u_sm;      // this CTA's slice of u (shared memory)
   unsigned shift, mask, rank_, size_;
   long long epoch;
+  unsigned long long *prof;  // phase timing in shared memory (null: off), see phase_tick
   __device__ __forceinline__ unsigned rank() const { return rank_; }
   __device__ __forceinline__ unsigned size() const { return size_; }
   // hardware cluster barrier: arrive has release and wait acquire semantics
@@ -263,8 +287,10 @@ struct ClusterGrp {
   __device__ __forceinline__ bool sync(int *) {
     cg::this_cluster().sync();
     ++epoch;
+    phase_tick(prof, rank_ == 0);
     return true;
   }
+  __device__ __forceinline__ void set_kind(int k) const { phase_kind(prof, k); }
   __device__ __forceinline__ long long barriers() const { return epoch; }
   __device__ __forceinline__ double *up(int j) const {
     return cg::this_cluster().map_shared_rank(u_sm, j >> shift) + (j & mask);
@@ -830,9 +856,24 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
 // the barrier after the last color is left to the caller.  Returns false on
 // barrier failure.
 template <typename TV, typename GRP>
+__device__ bool inner_sweeps_stream(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
+                                    Counters &C, const ZStore &Z);
+
+// the sweep's barrier intervals are charged to the sweep kind (phase timing)
+template <typename TV, typename GRP>
 __device__ bool inner_sweeps(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
                              Counters &C, const ZStore &Z) {
-  if (A.resident) return inner_sweeps_res<TV>(A, Gp, s_ok, g, ssor, acc, C, Z);
+  Gp.set_kind(PK_SWEEP);
+  const bool ok = A.resident ? inner_sweeps_res<TV>(A, Gp, s_ok, g, ssor, acc, C, Z)
+                             : inner_sweeps_stream<TV>(A, Gp, s_ok, g, ssor, acc, C, Z);
+  Gp.set_kind(PK_OTHER);
+  return ok;
+}
+
+// rows streamed from global memory (no row cache)
+template <typename TV, typename GRP>
+__device__ bool inner_sweeps_stream(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
+                                    Counters &C, const ZStore &Z) {
   const TV *a = ahat<TV>(A);
   const int lane = threadIdx.x & 31;
   const double om = A.omega;
@@ -1060,13 +1101,14 @@ template <typename GRP>
 __device__ __forceinline__ GRP make_group(const KArgs &A);
 template <>
 __device__ __forceinline__ GridGrp make_group<GridGrp>(const KArgs &A) {
-  return GridGrp{&A.ctl->bar, &A.ctl->status, 0ull, A.u, A.timeout_ns, A.stall_barrier};
+  return GridGrp{&A.ctl->bar, &A.ctl->status, 0ull, A.u, A.timeout_ns, A.stall_barrier, nullptr};
 }
 template <>
 __device__ __forceinline__ ClusterGrp make_group<ClusterGrp>(const KArgs &A) {
   extern __shared__ double dyn_smem[];
   cg::cluster_group cl = cg::this_cluster();
-  return ClusterGrp{dyn_smem, (unsigned)A.u_shift, (1u << A.u_shift) - 1u, cl.block_rank(), cl.num_blocks(), 0};
+  return ClusterGrp{dyn_smem, (unsigned)A.u_shift, (1u << A.u_shift) - 1u, cl.block_rank(), cl.num_blocks(), 0,
+                    nullptr};
 }
 
 template <int METH, typename TV, typename GRP>
@@ -1074,6 +1116,14 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
   __shared__ double sred[8 * KWPB];
   __shared__ int s_ok;
   GRP Gp = make_group<GRP>(A);
+  __shared__ unsigned long long s_prof[6];
+  if (A.prof) {
+    if (threadIdx.x == 0) {
+      s_prof[0] = globaltimer();
+      for (int k = 1; k < 6; ++k) s_prof[k] = 0;
+    }
+    Gp.prof = s_prof;
+  }
   const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
   const bool cta0 = Gp.rank() == 0 && threadIdx.x == 0;
   const int m = A.m, n = A.n;
@@ -1098,6 +1148,8 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
     if (cta0) {
       A.ctl->passes = Cn.passes;
       A.ctl->barriers = Gp.barriers();
+      if (A.prof)
+        for (int k = 0; k < 4; ++k) A.ctl->phase_ns[k] = s_prof[2 + k];
     }
     Gp.sync(&s_ok);  // no CTA of a cluster may exit while peers read its shared memory
     return;
@@ -1301,6 +1353,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         // z_k = B v_k (u is zero here)
         if (!inner_sweeps<TV>(A, Gp, &s_ok, vin, false, nullptr, Cn, Z)) return;
         const double *uwv = A.uw;
+        Gp.set_kind(PK_PROD);
         if (A.wy) {  // B = A_hat^T C: w-space image in FP64
           ++Cn.cols;
           csc_products(Gp, A, A.z, A.uw);
@@ -1338,6 +1391,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         __syncthreads();
         }
         double wn2 = 0.0;
+        Gp.set_kind(PK_GS);  // (with the row product w = A_hat z above, which has no barrier of its own)
         for (int pass = 0; pass < 2; ++pass) {
           double *h = pass == 0 ? A.h1 : A.h2;
           // partial dots (w, v_i) over this CTA's rows: lanes over 32 basis
@@ -1480,6 +1534,7 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
           }
         }
         __syncthreads();
+        Gp.set_kind(PK_OTHER);
         const double ghn = s_rot[0], rr = s_rot[1];
         if (!(rr > 0.0) || !isfinite(rr)) { reason = EXIT_BREAK; break; }
         ghk = ghn;
@@ -1678,6 +1733,8 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
     A.ctl->rows = Cn.rows;
     A.ctl->cols = Cn.cols;
     A.ctl->basis = Cn.basis;
+    if (A.prof)
+      for (int k = 0; k < 4; ++k) A.ctl->phase_ns[k] = s_prof[2 + k];
     A.ctl->barriers = Gp.barriers();
     A.ctl->iters = k;
     A.ctl->restarts = restarts;
@@ -2050,6 +2107,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   ctx->stats.csc_passes += h->cols;
   ctx->stats.barriers += h->barriers;
   ctx->stats.basis_passes += h->basis;
+  for (int k = 0; k < 4; ++k) ctx->stats.phase_ms[k] += 1e-6 * (double)h->phase_ns[k];
   ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
     ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
@@ -2130,6 +2188,7 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.ctl = (KrylovCtl *)ctx->kctl;
   A.timeout_ns = ctx->wait_limit_ns;
   A.stall_barrier = (unsigned long long)ctx->stall_barrier;
+  A.prof = ctx->phase_timing;
   return A;
 }
 

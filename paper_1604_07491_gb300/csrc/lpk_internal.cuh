@@ -103,6 +103,7 @@ struct lpk_ctx {
   int last_resident = 0;         // the last launch cached the rows
   unsigned long long wait_limit_ns = 5000000000ull;  // bound of every grid-barrier wait
   long long stall_barrier = 0;   // testing: grid barrier CTA 0 does not arrive at (0: none)
+  int phase_timing = 0;          // persistent kernel: time its barrier intervals by phase kind
 
   // problems prepared on this context (freed with it)
   std::vector<lpk_problem *> problems;

@@ -27,7 +27,7 @@ NE_SSOR, NE_SOR = 0, 1
 
 # every symbol include/lpk.h declares
 EXPORTS = ["lpk_create", "lpk_destroy", "lpk_last_error", "lpk_default_options", "lpk_get_stats",
-           "lpk_reset_stats", "lpk_set_exec", "lpk_set_wait_limit", "lpk_prepare",
+           "lpk_reset_stats", "lpk_set_exec", "lpk_set_wait_limit", "lpk_set_phase_timing", "lpk_prepare",
            "lpk_problem_free", "lpk_problem_dims", "lpk_problem_coloring", "lpk_scale_rows",
            "lpk_spmv", "lpk_sweep", "lpk_ne_solve", "lpk_ne_solve_noalloc", "lpk_ls_solve", "lpk_lp_solve",
            "lpk_lp_solve_batch", "lpk_server_default_config", "lpk_server_create", "lpk_server_destroy",
@@ -81,10 +81,12 @@ class Stats(C.Structure):
                 ("krylov_iters", C.c_int64), ("sweep_passes", C.c_int64), ("row_passes", C.c_int64),
                 ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
                 ("last_resident", C.c_int32), ("basis_passes", C.c_int64), ("spmv_launches", C.c_int64),
-                ("spmv_ms", C.c_double)]
+                ("spmv_ms", C.c_double), ("phase_ms", C.c_double * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
 
 
 class ServerConfig(C.Structure):
@@ -135,6 +137,7 @@ def load():
         "lpk_reset_stats": (I32, [P]),
         "lpk_set_exec": (I32, [P, I32, I32]),
         "lpk_set_wait_limit": (I32, [P, D, I64]),
+        "lpk_set_phase_timing": (I32, [P, I32]),
         "lpk_prepare": (I32, [P, C.POINTER(Matrix), C.c_uint64, C.POINTER(P)]),
         "lpk_problem_free": (None, [P]),
         "lpk_problem_dims": (I32, [P, P, P, P, P]),
@@ -251,6 +254,11 @@ class Context:
         """Bound of every grid-barrier wait; test_stall_barrier (testing only)
         makes every wait on that grid barrier run out (lpk_set_wait_limit)."""
         _check(self._h, load().lpk_set_wait_limit(self._h, float(seconds), int(test_stall_barrier)))
+
+    def set_phase_timing(self, on=True):
+        """Time the persistent kernel's barrier intervals by phase kind
+        (stats()["phase_ms"]; lpk_set_phase_timing)."""
+        _check(self._h, load().lpk_set_phase_timing(self._h, int(bool(on))))
 
     def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
         """Krylov kernel path: EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER or EXEC_BATCH
