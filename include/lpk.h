@@ -170,6 +170,8 @@ typedef struct lpk_stats {
                                  phases, [2] AB-GMRES/BA-GMRES orthogonalisation
                                  (with the product w = A_hat z before it),
                                  [3] the w-space image A_hat^T z */
+  int32_t last_u_global;      /* 1: the last cluster launch kept u in global memory */
+  int32_t reserved;
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.
@@ -191,14 +193,20 @@ typedef struct lpk_stats {
  *                    at solve time if u does not fit in 16 CTAs.
  * Or-ing LPK_EXEC_NO_RESIDENT disables the shared-memory row cache (by
  * default each warp keeps the column indices and values of its rows in shared
- * memory for the whole launch when they fit).
+ * memory for the whole launch when they fit).  On the cluster path the sweep
+ * vector u lives in the CTAs' shared memory or in global memory (L2): by
+ * default in global memory when a color carries 512 or more entries per CTA
+ * (the autotuner, in LPK_EXEC_AUTO, times both); or-ing LPK_EXEC_U_SHARED or
+ * LPK_EXEC_U_GLOBAL fixes the choice.
  * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
 typedef enum lpk_exec {
   LPK_EXEC_AUTO = 0,
   LPK_EXEC_GRID = 1,
   LPK_EXEC_CLUSTER = 2,
   LPK_EXEC_BATCH = 3,
-  LPK_EXEC_NO_RESIDENT = 4
+  LPK_EXEC_NO_RESIDENT = 4,
+  LPK_EXEC_U_SHARED = 8,
+  LPK_EXEC_U_GLOBAL = 16
 } lpk_exec;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream` (a

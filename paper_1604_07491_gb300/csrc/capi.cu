@@ -150,21 +150,25 @@ LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out) {
   *out = ctx->stats;
   out->last_cluster_size = ctx->last_cluster;
   out->last_resident = ctx->last_resident;
+  out->last_u_global = ctx->last_u_global;
   return LPK_OK;
 }
 
 LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size) {
   if (!ctx) return LPK_INVALID_ARG;
   const int no_res = (exec & LPK_EXEC_NO_RESIDENT) != 0;
-  exec &= ~LPK_EXEC_NO_RESIDENT;
-  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_BATCH ||
+  const int ush = (exec & LPK_EXEC_U_SHARED) != 0, ugl = (exec & LPK_EXEC_U_GLOBAL) != 0;
+  exec &= ~(LPK_EXEC_NO_RESIDENT | LPK_EXEC_U_SHARED | LPK_EXEC_U_GLOBAL);
+  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_BATCH || (ush && ugl) ||
       !(cluster_size == 0 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8 || cluster_size == 16)) {
-    ctx->err = "lpk_set_exec: exec must be 0..3 and cluster_size 0, 2, 4, 8 or 16";
+    ctx->err = "lpk_set_exec: exec must be 0..3 (with at most one of U_SHARED, U_GLOBAL) and cluster_size 0, 2, 4, 8 "
+               "or 16";
     return LPK_INVALID_ARG;
   }
   ctx->cluster_mode = exec;
   ctx->cluster_size_override = cluster_size;
   ctx->resident_mode = no_res;
+  ctx->u_place = ush ? 1 : ugl ? 2 : 0;
   return LPK_OK;
 }
 

@@ -89,6 +89,7 @@ struct KArgs {
   int method;
   int max_restarts;
   int u_shift;                     // cluster mode: 2^u_shift entries of u per CTA
+  int u_global;                    // cluster mode: u in global memory (A.u) instead of shared memory
   int rw;                          // row slots per warp in shared memory
   int z_off;                       // byte offsets of the shared-memory blocks (see SmemPlan)
   int gs_off, desc_off, val_off, rs_off, cum_off, col_off;
@@ -278,6 +279,8 @@ struct GridGrp {
 struct ClusterGrp {
   double *u_sm;      // this CTA's slice of u (shared memory)
   unsigned shift, mask, rank_, size_;
+  unsigned lsize;    // log2 of the cluster size
+  double *ug;        // u in global memory instead (null: u in distributed shared memory)
   long long epoch;
   unsigned long long *prof;  // phase timing in shared memory (null: off), see phase_tick
   __device__ __forceinline__ unsigned rank() const { return rank_; }
@@ -292,18 +295,38 @@ struct ClusterGrp {
   }
   __device__ __forceinline__ void set_kind(int k) const { phase_kind(prof, k); }
   __device__ __forceinline__ long long barriers() const { return epoch; }
+  // u is interleaved over the CTAs: entry j lives in CTA j mod size, slot
+  // j / size, so the consecutive columns of a row spread over every CTA's
+  // shared memory instead of crowding one (a row of the assignment LP spans
+  // 196 consecutive columns).  Plain loads: the cluster barrier between
+  // phases is a compiler memory barrier, and within a phase no entry a warp
+  // reads is written by anyone else.
   __device__ __forceinline__ double *up(int j) const {
-    return cg::this_cluster().map_shared_rank(u_sm, j >> shift) + (j & mask);
+    return cg::this_cluster().map_shared_rank(u_sm, j & (size_ - 1)) + (j >> lsize);
   }
-  __device__ __forceinline__ double uld(int j) const { return *(volatile double *)up(j); }
-  __device__ __forceinline__ void ust(int j, double v) const { *up(j) = v; }
+  // With ug, u lives in global memory (L2) and the cluster keeps only its
+  // hardware barrier: a row's gathers and scatters then go to L2, whose
+  // random-access throughput is far above that of distributed shared memory
+  // (about one remote access per three cycles per SM, measured), which
+  // matters when a color carries thousands of entries per CTA.
+  __device__ __forceinline__ double uld(int j) const { return ug ? __ldcg(ug + j) : *up(j); }
+  __device__ __forceinline__ void ust(int j, double v) const {
+    if (ug) ug[j] = v;
+    else *up(j) = v;
+  }
   __device__ __forceinline__ float2 uld2(int j) const {
-    const unsigned long long b = *(volatile unsigned long long *)up(j);
-    return as_dw(b);
+    return ug ? __ldcg(reinterpret_cast<const float2 *>(ug) + j) : *reinterpret_cast<const float2 *>(up(j));
   }
-  __device__ __forceinline__ void ust2(int j, float2 v) const { *reinterpret_cast<float2 *>(up(j)) = v; }
-  __device__ __forceinline__ void uzero(int) const {
-    for (unsigned i = threadIdx.x; i <= mask; i += blockDim.x) u_sm[i] = 0.0;
+  __device__ __forceinline__ void ust2(int j, float2 v) const {
+    if (ug) reinterpret_cast<float2 *>(ug)[j] = v;
+    else *reinterpret_cast<float2 *>(up(j)) = v;
+  }
+  __device__ __forceinline__ void uzero(int n) const {
+    if (ug) {
+      for (int j = rank_ * blockDim.x + threadIdx.x; j < n; j += size_ * blockDim.x) ug[j] = 0.0;
+    } else {
+      for (unsigned i = threadIdx.x; i <= mask; i += blockDim.x) u_sm[i] = 0.0;
+    }
   }
 };
 
@@ -1107,8 +1130,9 @@ template <>
 __device__ __forceinline__ ClusterGrp make_group<ClusterGrp>(const KArgs &A) {
   extern __shared__ double dyn_smem[];
   cg::cluster_group cl = cg::this_cluster();
-  return ClusterGrp{dyn_smem, (unsigned)A.u_shift, (1u << A.u_shift) - 1u, cl.block_rank(), cl.num_blocks(), 0,
-                    nullptr};
+  const unsigned cs = cl.num_blocks();
+  return ClusterGrp{dyn_smem, (unsigned)A.u_shift, (1u << A.u_shift) - 1u, cl.block_rank(), cs,
+                    (unsigned)(__ffs((int)cs) - 1), A.u_global ? A.u : nullptr, 0, nullptr};
 }
 
 template <int METH, typename TV, typename GRP>
@@ -1983,6 +2007,18 @@ int batch_cluster(const DevProblem &P, int f32, bool allow_resident) {
   return 0;
 }
 
+// Where the cluster path keeps u: in the CTAs' shared memory (lowest latency)
+// or in global memory (L2: far higher random-access throughput).  The
+// context's setting, else the autotuned choice, else global when a color
+// carries 512 or more entries per CTA on average.
+int u_global_for(lpk_ctx *ctx, const DevProblem &P, int cs) {
+  if (ctx->u_place == 1) return 0;
+  if (ctx->u_place == 2) return 1;
+  if (ctx->cluster_mode == 0 && P.tuned) return P.tuned_ug;
+  const long long per = P.n_colors > 0 && cs > 0 ? P.nnz / ((long long)P.n_colors * cs) : 0;
+  return per >= 512 ? 1 : 0;
+}
+
 int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int f32, int *shift) {
   int mode, csov;
   exec_mode(ctx, P, &mode, &csov);
@@ -2031,7 +2067,8 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       int s2 = shift;
       while ((1ll << s2) * use_cs < P.n) ++s2;
       if (s2 > MAX_SHIFT) { use_cs = 0; break; }
-      const SmemPlan L = plan_smem(P, use_cs, sizeof(double) << s2, f32 ? 4 : 8, ctx->resident_mode == 0);
+      const int ug = u_global_for(ctx, P, use_cs);
+      const SmemPlan L = plan_smem(P, use_cs, ug ? 0 : sizeof(double) << s2, f32 ? 4 : 8, ctx->resident_mode == 0);
       smem = L.total;
       if (smem > SMEM_LIMIT) continue;
       LPK_CUDA_TRY(ctx, prepare_fn(cfn));
@@ -2049,6 +2086,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
       if (cudaOccupancyMaxActiveClusters(&nclusters, cfn, &cfg) == cudaSuccess && nclusters > 0) {
         shift = s2;
         A.u_shift = s2;
+        A.u_global = ug;
         apply_plan(A, L);
         break;
       }
@@ -2081,8 +2119,10 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
     }
     apply_plan(A, L);
     A.u_shift = 0;
+    A.u_global = 0;
   }
   ctx->last_resident = A.resident;
+  ctx->last_u_global = A.u_global;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->kctl, 0, sizeof(KrylovCtl), ctx->stream));
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   LPK_COUNT(ctx);
@@ -2121,19 +2161,17 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
 // fastest for the problem.  Candidates: grid, clusters of 16, 8 and 4 CTAs
 // (each with the shared-memory row cache when it fits).
 lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
-  const int cands[4][2] = {{1, 0}, {2, 16}, {2, 8}, {2, 4}};
-  // AB-GMRES: the cost of the grid path grows with the basis (reductions over
-  // every SM's partials), which a probe of a few iterations does not see; the
-  // grid is taken only when no cluster can hold the problem
-  const bool abg = base.method == M_ABG || base.method == M_BAG;
-  const int save_mode = ctx->cluster_mode, save_cs = ctx->cluster_size_override;
+  // candidates: the grid; clusters of 16, 8 and 4 CTAs with u in shared
+  // memory (u_place 1) or in global memory (u_place 2)
+  const int cands[7][3] = {{1, 0, 0}, {2, 16, 1}, {2, 16, 2}, {2, 8, 1}, {2, 8, 2}, {2, 4, 1}, {2, 4, 2}};
+  const int save_mode = ctx->cluster_mode, save_cs = ctx->cluster_size_override, save_up = ctx->u_place;
   const lpk_stats save_stats = ctx->stats;
   double best = 1e300;
-  int bm = 1, bcs = 0;
-  for (int i = 0; i < 4; ++i) {
-    if (abg && i == 0) continue;
+  int bm = 1, bcs = 0, bug = 0;
+  for (int i = 0; i < 7; ++i) {
     ctx->cluster_mode = cands[i][0];
     ctx->cluster_size_override = cands[i][1];
+    ctx->u_place = cands[i][2];
     KArgs A = base;
     A.maxit = 12;
     A.tol = 0.0;
@@ -2144,6 +2182,7 @@ lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
     if (st == LPK_TIMEOUT) {
       ctx->cluster_mode = save_mode;
       ctx->cluster_size_override = save_cs;
+      ctx->u_place = save_up;
       return st;
     }
     if (st != LPK_OK || (cands[i][0] == 2 && ctx->last_cluster != cands[i][1])) continue;
@@ -2154,14 +2193,17 @@ lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
       best = us;
       bm = cands[i][0];
       bcs = cands[i][1];
+      bug = cands[i][2] == 2 ? 1 : 0;
     }
   }
   ctx->cluster_mode = save_mode;
   ctx->cluster_size_override = save_cs;
+  ctx->u_place = save_up;
   ctx->stats = save_stats;
   P.tuned = 1;
   P.tuned_mode = bm;
   P.tuned_cs = bcs;
+  P.tuned_ug = bug;
   return LPK_OK;
 }
 

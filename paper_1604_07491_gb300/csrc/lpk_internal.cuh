@@ -54,8 +54,10 @@ struct DevProblem {
   std::vector<int> rp_h;         // host copy of rp (sizes the shared-memory row cache)
 
   // execution path chosen by the autotuner (first solve on this problem)
-  int tuned = 0, tuned_mode = 0, tuned_cs = 0;
-  double tuned_us[4] = {0, 0, 0, 0};  // time per Krylov iteration of grid, cluster 16, 8, 4
+  int tuned = 0, tuned_mode = 0, tuned_cs = 0, tuned_ug = 0;
+  // time per Krylov iteration of the grid and of clusters of 16, 8, 4 CTAs
+  // with u in shared / global memory (autotune)
+  double tuned_us[7] = {0, 0, 0, 0, 0, 0, 0};
 
   cudaStream_t stream = nullptr;  // the owning context's stream (frees are ordered on it)
 
@@ -101,6 +103,8 @@ struct lpk_ctx {
   int last_cluster = 0;          // cluster size of the last launch (0: grid)
   int resident_mode = 0;         // 0: rows cached in shared memory when they fit, 1: never
   int last_resident = 0;         // the last launch cached the rows
+  int u_place = 0;               // cluster path: 0 by the problem, 1 u in shared memory, 2 in global memory
+  int last_u_global = 0;         // the last cluster launch kept u in global memory
   unsigned long long wait_limit_ns = 5000000000ull;  // bound of every grid-barrier wait
   long long stall_barrier = 0;   // testing: grid barrier CTA 0 does not arrive at (0: none)
   int phase_timing = 0;          // persistent kernel: time its barrier intervals by phase kind

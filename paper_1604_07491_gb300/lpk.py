@@ -22,6 +22,7 @@ STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREA
           10: "CUDA_ERROR"}
 MRNE, CGNE, ABGMRES = 0, 1, 2
 EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER, EXEC_BATCH, EXEC_NO_RESIDENT = 0, 1, 2, 3, 4
+EXEC_U_SHARED, EXEC_U_GLOBAL = 8, 16
 FP64, MIXED = 0, 1
 NE_SSOR, NE_SOR = 0, 1
 
@@ -81,7 +82,8 @@ class Stats(C.Structure):
                 ("krylov_iters", C.c_int64), ("sweep_passes", C.c_int64), ("row_passes", C.c_int64),
                 ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
                 ("last_resident", C.c_int32), ("basis_passes", C.c_int64), ("spmv_launches", C.c_int64),
-                ("spmv_ms", C.c_double), ("phase_ms", C.c_double * 4)]
+                ("spmv_ms", C.c_double), ("phase_ms", C.c_double * 4), ("last_u_global", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
@@ -262,7 +264,8 @@ class Context:
 
     def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
         """Krylov kernel path: EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER or EXEC_BATCH
-        (cluster size 0/2/4/8/16; or-ing EXEC_NO_RESIDENT disables the row cache)."""
+        (cluster size 0/2/4/8/16; or-ing EXEC_NO_RESIDENT disables the row cache,
+        EXEC_U_SHARED / EXEC_U_GLOBAL fix where the cluster path keeps u)."""
         _check(self._h, load().lpk_set_exec(self._h, exec_mode, cluster_size))
 
 

@@ -51,12 +51,21 @@ def ctx_grid(lpk):
     c.close()
 
 
-@pytest.fixture(params=["auto", "grid"])
-def pctx(request, ctx, ctx_grid):
-    """Both execution paths of the persistent kernel: auto picks the cluster
-    path (hardware cluster barrier, u in distributed shared memory) for every
-    size used here."""
-    return ctx if request.param == "auto" else ctx_grid
+@pytest.fixture(scope="module")
+def ctx_cluster_global(lpk):
+    """A context forced onto the cluster path with u in global memory (L2)."""
+    c = lpk.Context(0)
+    c.set_exec(lpk.EXEC_CLUSTER | lpk.EXEC_U_GLOBAL)
+    yield c
+    c.close()
+
+
+@pytest.fixture(params=["auto", "grid", "cluster_u_global"])
+def pctx(request, ctx, ctx_grid, ctx_cluster_global):
+    """The execution paths of the persistent kernel: auto (the autotuner's
+    pick among the grid and clusters with u in shared or global memory), the
+    grid path, and the cluster path with u in global memory."""
+    return {"auto": ctx, "grid": ctx_grid, "cluster_u_global": ctx_cluster_global}[request.param]
 
 
 def certs(lp, x, y, s):
