@@ -21,7 +21,7 @@ __device__ __forceinline__ double group_sum(double v) {
 // Square roots and divisions are multi-instruction FP64 sequences, and FP64
 // is scarce on this GPU: d is taken once per column (k_sqrt), 1 / rho once per
 // row, and every entry is (a_ij d_j) * (1 / rho_i) -- within an ulp or two of
-// the quotient.
+// the quotient.  The CSC copy is a gather of the CSR entries.
 __global__ void k_sqrt(int n, const double *__restrict__ d2, double *__restrict__ d) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n) d[j] = sqrt(d2[j]);
@@ -30,8 +30,7 @@ __global__ void k_sqrt(int n, const double *__restrict__ d2, double *__restrict_
 template <int LPR>
 __global__ void k_scale(int m, const int *__restrict__ rp, const int *__restrict__ ci,
                         const double *__restrict__ a, const double *__restrict__ d,
-                        double *__restrict__ ah64, float *__restrict__ ah32, double *__restrict__ rho,
-                        double *__restrict__ rinv) {
+                        double *__restrict__ ah64, float *__restrict__ ah32, double *__restrict__ rho) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = (int)(t / LPR), sub = (int)(t % LPR);
   int k0 = 0, k1 = 0;
@@ -53,20 +52,15 @@ __global__ void k_scale(int m, const int *__restrict__ rp, const int *__restrict
     ah64[k] = v;
     ah32[k] = (float)v;
   }
-  if (sub == 0) {
-    rho[r] = nr;
-    rinv[r] = ri;
-  }
+  if (sub == 0) rho[r] = nr;
 }
 
-// the same scaled entries in CSC order: identical expression, so bitwise equal
-__global__ void k_scale_csc(int n, const int *__restrict__ cp, const int *__restrict__ ri,
-                            const double *__restrict__ at, const double *__restrict__ d,
-                            const double *__restrict__ rinv, double *__restrict__ aht) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double dj = d[j];
-  for (int q = cp[j]; q < cp[j + 1]; ++q) aht[q] = (__ldg(at + q) * dj) * __ldg(rinv + __ldg(ri + q));
+// the same scaled entries in CSC order, copied from their CSR positions (so
+// bitwise equal); a thread per entry, whatever the column lengths
+__global__ void k_scale_csc(long long nnz, const int *__restrict__ cpos, const double *__restrict__ ah64,
+                            double *__restrict__ aht) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nnz) aht[q] = ah64[__ldg(cpos + q)];
 }
 
 // Sparse products with LPR lanes per row (or column): short rows leave most
@@ -179,14 +173,14 @@ void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2) {
   if (P.n > 0) LPK_LAUNCH(ctx, k_sqrt, tblk(P.n), TPB, 0, s, P.n, d2, P.dcol);
   if (P.m > 0) {
     switch (lanes_for(P.nnz, P.m)) {
-      case 2: LPK_LAUNCH(ctx, k_scale<2>, gblk(P.m, 2), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
-      case 4: LPK_LAUNCH(ctx, k_scale<4>, gblk(P.m, 4), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
-      case 8: LPK_LAUNCH(ctx, k_scale<8>, gblk(P.m, 8), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
-      case 16: LPK_LAUNCH(ctx, k_scale<16>, gblk(P.m, 16), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
-      default: LPK_LAUNCH(ctx, k_scale<32>, gblk(P.m, 32), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho, P.rinv); break;
+      case 2: LPK_LAUNCH(ctx, k_scale<2>, gblk(P.m, 2), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho); break;
+      case 4: LPK_LAUNCH(ctx, k_scale<4>, gblk(P.m, 4), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho); break;
+      case 8: LPK_LAUNCH(ctx, k_scale<8>, gblk(P.m, 8), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho); break;
+      case 16: LPK_LAUNCH(ctx, k_scale<16>, gblk(P.m, 16), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho); break;
+      default: LPK_LAUNCH(ctx, k_scale<32>, gblk(P.m, 32), TPB, 0, s, P.m, P.rp, P.ci, P.a, P.dcol, P.ah64, P.ah32, P.rho); break;
     }
   }
-  if (P.n > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.n), TPB, 0, s, P.n, P.cp, P.ri, P.at, P.dcol, P.rinv, P.aht);
+  if (P.nnz > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.nnz), TPB, 0, s, P.nnz, P.cpos, P.ah64, P.aht);
 }
 void spmv_csr(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y, const double *add, double sign) {
   if (P.m <= 0) return;

@@ -40,7 +40,6 @@ struct DevProblem {
   double *ah64 = nullptr;        // [nnz] A_hat = D_cal^-1 A D, FP64
   float *ah32 = nullptr;         // [nnz] A_hat, FP32 copy for the mixed inner sweeps
   double *rho = nullptr;         // [m]   row norms of A D
-  double *rinv = nullptr;        // [m]   1 / rho (0 for empty rows)
   double *dcol = nullptr;        // [n]   d = sqrt(d2) of the last scaling
 
   // CSC of the permuted matrix (row indices are sweep positions, sorted)
@@ -48,6 +47,7 @@ struct DevProblem {
   int *ri = nullptr;             // [nnz]
   double *at = nullptr;          // [nnz]
   double *aht = nullptr;         // [nnz] A_hat in CSC order (bitwise equal to ah64)
+  int *cpos = nullptr;           // [nnz] CSR position of each CSC entry
 
   int *color_ptr = nullptr;      // [n_colors+1] device copy
   std::vector<int> color_ptr_h;  // host copy

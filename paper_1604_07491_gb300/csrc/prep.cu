@@ -236,30 +236,36 @@ __global__ void k_perm_fill(int mr, const int *perm, const int *in_row_of_red, c
 }
 
 // CSC of the permuted matrix: atomic fill, then sort every column by row
+// CSC entry q of the permuted matrix: row ri[q], value at[q], and cpos[q] the
+// position of the same entry in the CSR arrays
 __global__ void k_csc_fill(int mr, const int *rp, const int *ci, const double *a, int *cursor, int *ri,
-                           double *at) {
+                           double *at, int *cpos) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= mr) return;
   for (int k = rp[p]; k < rp[p + 1]; ++k) {
     int q = atomicAdd(&cursor[ci[k]], 1);
     ri[q] = p;
     at[q] = a[k];
+    cpos[q] = k;
   }
 }
-__global__ void k_csc_sort(int nr, const int *cp, int *ri, double *at) {
+__global__ void k_csc_sort(int nr, const int *cp, int *ri, double *at, int *cpos) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nr) return;
   for (int q = cp[j] + 1; q < cp[j + 1]; ++q) {  // insertion sort (columns are short)
     int r = ri[q];
     double v = at[q];
+    int k = cpos[q];
     int t = q - 1;
     while (t >= cp[j] && ri[t] > r) {
       ri[t + 1] = ri[t];
       at[t + 1] = at[t];
+      cpos[t + 1] = cpos[t];
       --t;
     }
     ri[t + 1] = r;
     at[t + 1] = v;
+    cpos[t + 1] = k;
   }
 }
 
@@ -299,7 +305,7 @@ void free_problem(DevProblem &P) {
   void *ptrs[] = {P.pos_of_in_row, P.in_row_of_pos, P.col_of_in, P.in_col_of, P.color_in, P.rp,
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
-                  P.gm_V,          P.ipm_buf,       P.rinv,      P.dcol};
+                  P.gm_V,          P.ipm_buf,       P.dcol,      P.cpos};
   for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }
@@ -476,7 +482,6 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah64, nnz));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.ah32, nnz));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rho, mr));
-  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.rinv, mr));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.dcol, nr));
   if (mr > 0) LPK_LAUNCH(ctx, k_perm_rowlen, nblk(mr), TPB, 0, st, mr, perm, rp_red, rlen);
   LPK_LAUNCH(ctx, k_scan<int>, 1, 1024, 0, st, mr, rlen, P.rp);
@@ -490,8 +495,9 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.aht, nnz));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.cp, cp_red, sizeof(int) * (nr + 1), cudaMemcpyDeviceToDevice, st));
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(cursor, cp_red, sizeof(int) * (nr > 0 ? nr : 1), cudaMemcpyDeviceToDevice, st));
-  if (mr > 0) LPK_LAUNCH(ctx, k_csc_fill, nblk(mr), TPB, 0, st, mr, P.rp, P.ci, P.a, cursor, P.ri, P.at);
-  if (nr > 0) LPK_LAUNCH(ctx, k_csc_sort, nblk(nr), TPB, 0, st, nr, P.cp, P.ri, P.at);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.cpos, nnz));
+  if (mr > 0) LPK_LAUNCH(ctx, k_csc_fill, nblk(mr), TPB, 0, st, mr, P.rp, P.ci, P.a, cursor, P.ri, P.at, P.cpos);
+  if (nr > 0) LPK_LAUNCH(ctx, k_csc_sort, nblk(nr), TPB, 0, st, nr, P.cp, P.ri, P.at, P.cpos);
   // ---- maps to the input numbering ------------------------------------------
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.pos_of_in_row, m));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.color_in, m));
