@@ -861,7 +861,7 @@ def run_bandwidth(args, wl, lpk, torch, dev, local, rank, world, barrier):
         "spmv_csr": {"ms": ms_a, "bytes": b_a, "gbs": ga, "frac": ga / hbm},
         "spmv_csc": {"ms": ms_t, "bytes": b_t, "gbs": gt, "frac": gt / hbm},
         "roofline": {"bound": "hbm", "achieved": ga, "peak": hbm, "unit": "GB/s", "frac": ga / hbm,
-                     "traffic": None, "kernel": "lpk_spmv (k_gather, k_spmv_csr, k_scatter)",
+                     "traffic": None, "kernel": "lpk_spmv (k_gather, k_seg_spmv + k_seg_fix, k_scatter)",
                      "peak_source": f"{src} hbm_gbs"},
         "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary(),
     }

@@ -171,15 +171,23 @@ typedef struct lpk_stats {
                                  (with the product w = A_hat z before it),
                                  [3] the w-space image A_hat^T z */
   int32_t last_u_global;      /* 1: the last cluster launch kept u in global memory */
-  int32_t reserved;
+  int32_t last_dataflow;      /* 1: the last grid launch ordered its sweep rows by
+                                 per-entry flags instead of a barrier per color */
+  int64_t tune_probes;        /* timing probes the autotuner launched */
+  int64_t tune_cache_hits;    /* problems whose path came from the tuning cache */
 } lpk_stats;
 
 /* Execution path of the persistent Krylov kernel.
  *  LPK_EXEC_AUTO:    on the first Krylov solve of each problem, a few
- *                    iterations of every path (grid; clusters of 16, 8, 4)
- *                    are timed on the actual system and the fastest is kept
- *                    for that problem (for AB-GMRES only the clusters, unless
- *                    none can hold the problem).
+ *                    iterations of every path (grid; clusters of 16, 8, 4
+ *                    CTAs with u in shared or in global memory) are timed on
+ *                    the actual system and the fastest is kept for that
+ *                    problem.  The choice is cached by problem shape (rows,
+ *                    columns, nonzeros, colors, longest row, solver, value
+ *                    precision, SM count) for the process; when the
+ *                    environment variable LPK_TUNE_CACHE names a file, the
+ *                    choices are appended to it and read back by later
+ *                    processes, so known shapes skip the probes.
  *  LPK_EXEC_GRID:    every SM, software grid barrier, u in global memory.
  *  LPK_EXEC_CLUSTER: the cluster path (LPK_INVALID_ARG at solve time if u does
  *                    not fit).
@@ -197,7 +205,17 @@ typedef struct lpk_stats {
  * vector u lives in the CTAs' shared memory or in global memory (L2): by
  * default in global memory when a color carries 512 or more entries per CTA
  * (the autotuner, in LPK_EXEC_AUTO, times both); or-ing LPK_EXEC_U_SHARED or
- * LPK_EXEC_U_GLOBAL fixes the choice.
+ * LPK_EXEC_U_GLOBAL fixes the choice.  On the grid path with the row cache,
+ * the sweeps of problems with 32 colors or more run in dataflow order: rows
+ * of one color share no column, so instead of a grid barrier after every
+ * color each row waits only for the rows before it that touch its columns
+ * (a flag per nonzero, released after the row's update of u and acquired
+ * before the next row reads u there; one barrier per pass).  Every row reads
+ * the same u values either way, so results are bitwise those of the barrier
+ * order.  Or-ing LPK_EXEC_COLOR_BARRIERS or LPK_EXEC_DATAFLOW fixes the
+ * choice (dataflow needs the row cache; without it the barriers are used).
+ * The dataflow order costs three ints per nonzero of device memory, taken on
+ * the problem's first dataflow launch and kept until lpk_free_problem.
  * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
 typedef enum lpk_exec {
   LPK_EXEC_AUTO = 0,
@@ -206,7 +224,9 @@ typedef enum lpk_exec {
   LPK_EXEC_BATCH = 3,
   LPK_EXEC_NO_RESIDENT = 4,
   LPK_EXEC_U_SHARED = 8,
-  LPK_EXEC_U_GLOBAL = 16
+  LPK_EXEC_U_GLOBAL = 16,
+  LPK_EXEC_COLOR_BARRIERS = 32,
+  LPK_EXEC_DATAFLOW = 64
 } lpk_exec;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream` (a
@@ -221,14 +241,18 @@ LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx);
 LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size);
 
 /* Failure detection of the grid path (the paper has no counterpart).  Every
- * wait of the persistent kernel's software grid barrier is bounded by
- * `seconds` of %globaltimer (default 5; must be > 0): when it runs out, the
- * CTA records LPK_TIMEOUT, every CTA leaves the kernel at its next barrier,
- * and the call returns LPK_TIMEOUT with the context still usable.
- * test_stall_barrier (testing only, 0 = off): in each grid-path launch, CTA 0
- * withholds its arrival at the grid barrier with that number (counted from 1
- * in the launch), so every wait on it runs out; this is how the timeout path
- * is exercised without faulting the GPU.  The cluster path's hardware
+ * wait of the persistent kernel's software grid barrier, and every row-flag
+ * wait of the dataflow sweeps, is bounded by `seconds` of %globaltimer
+ * (default 5; must be > 0): when it runs out, the thread records
+ * LPK_TIMEOUT, every CTA leaves the kernel at its next barrier (a row-flag
+ * wait gives up as soon as the status is set), and the call returns
+ * LPK_TIMEOUT with the context still usable.
+ * test_stall_barrier (testing only, 0 = off): k > 0: in each grid-path
+ * launch, CTA 0 withholds its arrival at the grid barrier with number k
+ * (counted from 1 in the launch); k < 0: in dataflow sweeps, CTA 0 publishes
+ * no row flag from sweep pass -k (counted from 1 in the launch) on.  Every
+ * wait on the withheld arrival or flags runs out; this is how the timeout
+ * paths are exercised without faulting the GPU.  The cluster path's hardware
  * barriers have no software wait and are not affected. */
 LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier);
 

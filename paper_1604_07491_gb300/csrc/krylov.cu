@@ -42,7 +42,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <string>
 #include <type_traits>
 #include <vector>
 
@@ -98,6 +100,11 @@ struct KArgs {
   int prof;                        // phase timing: CTA 0 charges each barrier interval to its phase kind
   unsigned long long timeout_ns;   // grid path: bound of every barrier wait
   unsigned long long stall_barrier;  // grid path, testing: barrier CTA 0 does not arrive at (0: none)
+  int stall_pass;                  // dataflow sweeps, testing: pass from which CTA 0 publishes no flag (0: none)
+  int flow;                        // grid path, rows cached: dataflow sweeps (see Flow)
+  const int *fl_prev, *fl_next;    // per CSR entry: the previous / next entry of its column (-1: none)
+  int *fl_flag;                    // per CSR entry: last pass written
+  int gk_off;                      // shared-memory offset of the slots' first CSR entries
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
@@ -128,6 +135,60 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// ---- dataflow order of the sweep rows (grid path, rows cached) ------------
+// Rows of one color share no column, so a row needs only the rows before it
+// in the sweep order that touch its columns -- for each of its entries, the
+// previous entry of the same column (the column's last writer).  Instead of a
+// grid barrier after every color, each lane waits for that entry's flag
+// (acquire) before it reads u at the column and publishes its own entry's
+// flag (release) after it writes u there.  Every row then reads exactly the
+// u values it reads with a barrier per color: the result is bitwise the same.
+// A pass is numbered from 1 within the launch; flag[k] = the last pass whose
+// update of entry k is written (zeroed when the launch starts).
+__device__ __forceinline__ int ld_acquire_i32(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i32(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct Flow {
+  const int *dep;    // per CSR entry: the entry this one follows in this pass (-1: none); null: barriers
+  int *flag;         // per CSR entry
+  const int *gk;     // this warp's slots: the row's first CSR entry
+  int pass;
+  int withhold;      // testing: this CTA does not publish (every wait on it runs out)
+  int *status;
+  unsigned long long timeout_ns;
+};
+
+// wait until the entry that entry k follows is written in this pass; bounded
+// by timeout_ns (then the launch's status becomes LPK_TIMEOUT), and given up
+// once another wait has failed
+__device__ __forceinline__ void flow_wait(const Flow &F, int k) {
+  const int d = __ldg(F.dep + k);
+  if (d < 0 || ld_acquire_i32(F.flag + d) >= F.pass) return;
+  unsigned it = 0;
+  unsigned long long t0 = 0;
+  while (ld_acquire_i32(F.flag + d) < F.pass) {
+    if ((++it & 63u) == 0u) {
+      if (*(volatile int *)F.status != 0) return;
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > F.timeout_ns) {
+        atomicCAS(F.status, 0, (int)LPK_TIMEOUT);
+        return;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void flow_post(const Flow &F, int k) {
+  if (!F.withhold) st_release_i32(F.flag + k, F.pass);
 }
 
 // ---- double-word (FP32 pair) arithmetic of the mixed-precision sweeps ------
@@ -383,6 +444,7 @@ struct ZStore {
   int *cum;      // [KWPB][nc + 1]
   void *vals;    // [entries of the CTA]   resident only (TV)
   int *cols;     // [entries of the CTA]   resident only
+  int *gk;       // [KWPB][rw]   dataflow only: first CSR entry of the slot's row
   int rw, nc;
   __device__ __forceinline__ int wi() const { return threadIdx.x >> 5; }
   __device__ __forceinline__ double *zw() const { return zs + wi() * rw; }
@@ -390,6 +452,7 @@ struct ZStore {
   __device__ __forceinline__ const int2 *dw() const { return desc + wi() * rw; }
   __device__ __forceinline__ const int *rw_rows() const { return rs + wi() * rw; }
   __device__ __forceinline__ const int *cw() const { return cum + wi() * (nc + 1); }
+  __device__ __forceinline__ const int *gkw() const { return gk + wi() * rw; }
 };
 
 __device__ __forceinline__ ZStore make_zstore(const KArgs &A) {
@@ -402,6 +465,7 @@ __device__ __forceinline__ ZStore make_zstore(const KArgs &A) {
   Z.cum = (int *)(dyn_smem_b + A.cum_off);
   Z.vals = (void *)(dyn_smem_b + A.val_off);
   Z.cols = (int *)(dyn_smem_b + A.col_off);
+  Z.gk = (int *)(dyn_smem_b + A.gk_off);
   Z.rw = A.rw;
   Z.nc = A.nc;
   return Z;
@@ -460,14 +524,19 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
   const TV *a = ahat<TV>(A);
   TV *vals = (TV *)Z.vals;
   int off = basew;
+  int *gkw = Z.gk + w * Z.rw;
   for (int sl = 0; sl < carry; ++sl) {
     const int2 kl = dw[sl];
     for (int t = lane; t < kl.y; t += 32) {
       Z.cols[off + t] = __ldg(A.ci + kl.x + t);
       vals[off + t] = __ldg(a + kl.x + t);
+      if (A.flow) A.fl_flag[kl.x + t] = 0;  // ordered before any wait by the barrier ahead of the first sweep
     }
     __syncwarp();
-    if (lane == 0) dw[sl] = make_int2(off, kl.y);
+    if (lane == 0) {
+      if (A.flow) gkw[sl] = kl.x;
+      dw[sl] = make_int2(off, kl.y);
+    }
     off += kl.y;
   }
   __syncwarp();
@@ -530,9 +599,12 @@ __device__ __forceinline__ double row_update(const GRP &Gp, const KArgs &A, cons
 }
 
 // Row update from the shared-memory row cache (resident rows).
+// With F.dep (dataflow sweeps), entry t of the row is CSR entry kg0 + t: each
+// lane waits for its entries' predecessors before reading u and publishes
+// its entries after writing u.
 template <typename TV, typename GRP>
 __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, const int *cols, int e0, int len,
-                                                 double g, double om) {
+                                                 double g, double om, const Flow &F, int kg0) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
   if (len <= 32 * RCR) {
@@ -544,6 +616,11 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
         cv[e] = cols[e0 + lane + 32 * e];
         av[e] = (double)vals[e0 + lane + 32 * e];
       }
+    if (F.dep) {
+#pragma unroll
+      for (int e = 0; e < RCR; ++e)
+        if (lane + 32 * e < len) flow_wait(F, kg0 + lane + 32 * e);
+    }
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) {
@@ -554,15 +631,22 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
     const double d = om * (g - s);
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
-      if (lane + 32 * e < len) Gp.ust(cv[e], uv[e] + d * av[e]);
+      if (lane + 32 * e < len) {
+        Gp.ust(cv[e], uv[e] + d * av[e]);
+        if (F.dep) flow_post(F, kg0 + lane + 32 * e);
+      }
     return d;
   }
-  for (int t = lane; t < len; t += 32) s += (double)vals[e0 + t] * Gp.uld(cols[e0 + t]);
+  for (int t = lane; t < len; t += 32) {
+    if (F.dep) flow_wait(F, kg0 + t);
+    s += (double)vals[e0 + t] * Gp.uld(cols[e0 + t]);
+  }
   s = warp_sum(s);
   const double d = om * (g - s);
   for (int t = lane; t < len; t += 32) {
     const int c = cols[e0 + t];
     Gp.ust(c, Gp.uld(c) + d * (double)vals[e0 + t]);
+    if (F.dep) flow_post(F, kg0 + t);
   }
   return d;
 }
@@ -577,7 +661,7 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
 template <typename TV, typename GRP>
 __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, const int *cols, const int2 *dw,
                                                const double *gsw, double *zw, int s0, int s1, double om,
-                                               bool firstpass, bool lastpass, double *acc) {
+                                               bool firstpass, bool lastpass, double *acc, const Flow &F) {
   constexpr int NB = sizeof(TV) == 4 ? 4 : 2, E = 2;  // FP64 values need twice the registers
   const int lane = threadIdx.x & 31;
   for (int sb = s0; sb < s1; sb += NB) {
@@ -600,6 +684,14 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
     // rows of this batch (warp-uniform): FP64 work is spent on them only, an
     // FP64 warp instruction being costly on this GPU
     const int nb = min(NB, s1 - sb);
+    // dataflow: the rows of a batch share a color, so none waits on another
+    if (F.dep) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) flow_wait(F, F.gk[sb + k] + lane + 32 * e);
+    }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
 #pragma unroll
@@ -627,7 +719,10 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
         const double d = om * (gr - sm[k]);
 #pragma unroll
         for (int e = 0; e < E; ++e)
-          if (cv[k][e] >= 0) Gp.ust(cv[k][e], uv[k][e] + d * av[k][e]);
+          if (cv[k][e] >= 0) {
+            Gp.ust(cv[k][e], uv[k][e] + d * av[k][e]);
+            if (F.dep) flow_post(F, F.gk[sl] + lane + 32 * e);
+          }
         if (lane == 0) {
           const double zn = firstpass ? d : zw[sl] + d;
           zw[sl] = zn;
@@ -682,7 +777,8 @@ __device__ __forceinline__ float2 row_update_dw(const GRP &Gp, const KArgs &A, c
 // one row from the shared-memory row cache
 template <typename GRP>
 __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *vals, const int *cols, int e0,
-                                                    int len, float2 g2, float2 om2, bool om1) {
+                                                    int len, float2 g2, float2 om2, bool om1, const Flow &F,
+                                                    int kg0) {
   const int lane = threadIdx.x & 31;
   float2 s = make_float2(0.f, 0.f);
   if (len <= 32 * RCR) {
@@ -695,6 +791,11 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
         cv[e] = cols[e0 + lane + 32 * e];
         av[e] = vals[e0 + lane + 32 * e];
       }
+    if (F.dep) {
+#pragma unroll
+      for (int e = 0; e < RCR; ++e)
+        if (lane + 32 * e < len) flow_wait(F, kg0 + lane + 32 * e);
+    }
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) uv[e] = Gp.uld2(cv[e]);
@@ -707,10 +808,16 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
     if (!om1) d = dw_mul(d, om2);
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
-      if (lane + 32 * e < len) Gp.ust2(cv[e], dw_add(uv[e], dw_mulf(d, av[e])));
+      if (lane + 32 * e < len) {
+        Gp.ust2(cv[e], dw_add(uv[e], dw_mulf(d, av[e])));
+        if (F.dep) flow_post(F, kg0 + lane + 32 * e);
+      }
     return d;
   }
-  for (int t = lane; t < len; t += 32) s = dw_add(s, dw_mulf(Gp.uld2(cols[e0 + t]), vals[e0 + t]));
+  for (int t = lane; t < len; t += 32) {
+    if (F.dep) flow_wait(F, kg0 + t);
+    s = dw_add(s, dw_mulf(Gp.uld2(cols[e0 + t]), vals[e0 + t]));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s = dw_add(s, shfl_xor_dw(s, o));
   float2 d = dw_add(g2, dw_neg(s));
@@ -718,6 +825,7 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
   for (int t = lane; t < len; t += 32) {
     const int c = cols[e0 + t];
     Gp.ust2(c, dw_add(Gp.uld2(c), dw_mulf(d, vals[e0 + t])));
+    if (F.dep) flow_post(F, kg0 + t);
   }
   return d;
 }
@@ -727,7 +835,7 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
 template <typename GRP>
 __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *vals, const int *cols,
                                                   const int2 *dw, const float2 *gs2, float2 *zw2, int s0, int s1,
-                                                  float2 om2, bool om1, bool firstpass) {
+                                                  float2 om2, bool om1, bool firstpass, const Flow &F) {
   constexpr int NB = 4, E = 2;
   const int lane = threadIdx.x & 31;
   for (int sb = s0; sb < s1; sb += NB) {
@@ -748,6 +856,13 @@ __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *va
           av[k][e] = vals[kl.x + t];
         }
       }
+    }
+    if (F.dep) {  // the rows of a batch share a color: none waits on another
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+          if (cv[k][e] >= 0) flow_wait(F, F.gk[sb + k] + lane + 32 * e);
     }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
@@ -776,7 +891,10 @@ __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *va
         if (!om1) d = dw_mul(d, om2);
 #pragma unroll
         for (int e = 0; e < E; ++e)
-          if (cv[k][e] >= 0) Gp.ust2(cv[k][e], dw_add(uv[k][e], dw_mulf(d, av[k][e])));
+          if (cv[k][e] >= 0) {
+            Gp.ust2(cv[k][e], dw_add(uv[k][e], dw_mulf(d, av[k][e])));
+            if (F.dep) flow_post(F, F.gk[sl] + lane + 32 * e);
+          }
         if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
       }
     }
@@ -785,6 +903,9 @@ __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *va
 
 // inner_sweeps with every row of the warp resident in shared memory: the only
 // global/distributed accesses of a color phase are the gather and scatter of u.
+// With A.flow (grid path) the colors of a pass are not separated by grid
+// barriers: rows wait on their entries' predecessors instead (see Flow), and
+// one barrier ends each pass.
 template <typename TV, typename GRP>
 __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
                                  Counters &C, const ZStore &Z) {
@@ -798,6 +919,29 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
   const TV *vals = (const TV *)Z.vals;
   const int *cols = Z.cols;
   const int nslots = cw[nc];
+  const long long pass0 = C.passes;
+  Flow F{nullptr, A.fl_flag, A.flow ? Z.gkw() : nullptr, 0, 0, &A.ctl->status, A.timeout_ns};
+  auto flow_pass = [&](int ps, bool backward) {
+    if (!A.flow) return;
+    F.dep = backward ? A.fl_next : A.fl_prev;
+    F.pass = (int)(pass0 + ps + 1);
+    F.withhold = A.stall_pass != 0 && blockIdx.x == 0 && F.pass >= A.stall_pass;
+  };
+  // a barrier between colors (per-color mode), or at the end of a pass
+  // (dataflow mode; none after the last pass, as in per-color mode)
+  auto color_end = [&](bool lastpass, int cc) -> bool {
+    if (A.flow ? (cc == nc - 1 && !lastpass) : !(lastpass && cc == nc - 1)) return Gp.sync(s_ok);
+    return true;
+  };
+  // dataflow: a failed wait sets the launch's status; every CTA reads it
+  // after the barrier that follows the sweep
+  auto flow_status = [&]() -> bool {
+    if (!A.flow) return true;
+    if (!Gp.sync(s_ok)) return false;
+    if (threadIdx.x == 0) *s_ok = *(volatile int *)&A.ctl->status == 0;
+    __syncthreads();
+    return *s_ok != 0;
+  };
   if constexpr (std::is_same<TV, float>::value) {
     // FP32 values: double-word rows; z and g slots hold double words, and the
     // (z, g) product of the last pass is formed when z is written out
@@ -810,22 +954,23 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
     for (int ps = 0; ps < passes; ++ps) {
       const bool backward = ssor && (ps & 1);
       const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+      flow_pass(ps, backward);
       for (int cc = 0; cc < nc; ++cc) {
         const int c = backward ? nc - 1 - cc : cc;
         if (A.short_rows) {
-          rows_res_short_dw(Gp, vals, cols, dw, gs2, zw2, cw[c], cw[c + 1], om2, om1, firstpass);
+          rows_res_short_dw(Gp, vals, cols, dw, gs2, zw2, cw[c], cw[c + 1], om2, om1, firstpass, F);
         } else {
           for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
             const int2 kl = dw[sl];
-            const float2 d = row_update_res_dw(Gp, vals, cols, kl.x, kl.y, gs2[sl], om2, om1);
+            const float2 d =
+                row_update_res_dw(Gp, vals, cols, kl.x, kl.y, gs2[sl], om2, om1, F, F.gk ? F.gk[sl] : 0);
             if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
           }
         }
-        if (!(lastpass && cc == nc - 1)) {
-          if (!Gp.sync(s_ok)) return false;
-        }
+        if (!color_end(lastpass, cc)) return false;
       }
     }
+    if (!flow_status()) return false;
     __syncwarp();
     for (int sl = lane; sl < nslots; sl += 32) {
       const double zr = dw_val(zw2[sl]);
@@ -843,15 +988,16 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
   for (int ps = 0; ps < passes; ++ps) {
     const bool backward = ssor && (ps & 1);
     const bool firstpass = ps == 0, lastpass = ps == passes - 1;
+    flow_pass(ps, backward);
     for (int cc = 0; cc < nc; ++cc) {
       const int c = backward ? nc - 1 - cc : cc;
       if (A.short_rows) {
-        rows_res_short<TV>(Gp, vals, cols, dw, gsw, zw, cw[c], cw[c + 1], om, firstpass, lastpass, acc);
+        rows_res_short<TV>(Gp, vals, cols, dw, gsw, zw, cw[c], cw[c + 1], om, firstpass, lastpass, acc, F);
       } else {
         for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
           const int2 kl = dw[sl];
           const double gr = gsw[sl];
-          const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om);
+          const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om, F, F.gk ? F.gk[sl] : 0);
           if (lane == 0) {
             const double zn = firstpass ? d : zw[sl] + d;
             zw[sl] = zn;
@@ -859,11 +1005,10 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
           }
         }
       }
-      if (!(lastpass && cc == nc - 1)) {
-        if (!Gp.sync(s_ok)) return false;
-      }
+      if (!color_end(lastpass, cc)) return false;
     }
   }
+  if (!flow_status()) return false;
   __syncwarp();
   for (int sl = lane; sl < nslots; sl += 32) A.z[rsw[sl]] = zw[sl];
   if (!acc) {
@@ -1901,6 +2046,7 @@ struct SmemPlan {
   size_t total = 0;
   int rw = 0, resident = 0, short_rows = 0;
   int z_off = 0, gs_off = 0, desc_off = 0, val_off = 0, rs_off = 0, cum_off = 0, col_off = 0;
+  int gk_off = -1;  // the slots' first CSR entries (dataflow sweeps), -1: none
 };
 
 // nonzeros of the busiest CTA when the rows are dealt round-robin by sweep
@@ -1920,7 +2066,8 @@ int max_row_len(const DevProblem &P) {
   return mx;
 }
 
-SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident) {
+SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident,
+                   bool flow = false) {
   SmemPlan L;
   const int GW = ctas * KWPB;
   L.rw = std::max(1, (P.m + GW - 1) / GW);  // rows per warp (round-robin by position)
@@ -1937,17 +2084,25 @@ SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bo
   L.total = off;
   if (allow_resident && (long long)P.rp_h.size() == (long long)P.m + 1) {
     const long long ent = max_cta_entries(P, ctas);
-    const int gs = take(sizeof(double) * KWPB * (size_t)L.rw);
-    const int vo = take((size_t)vbytes * ent);
-    const int co = take(sizeof(int) * ent);
-    if (off <= SMEM_LIMIT) {
-      L.resident = 1;
-      L.short_rows = max_row_len(P) <= 64;
-      L.gs_off = gs;
-      L.val_off = vo;
-      L.col_off = co;
-      L.total = off;
+    const size_t base = off;
+    // with the dataflow block if asked for and it fits, else without
+    for (int with_gk = flow ? 1 : 0; with_gk >= 0 && !L.resident; --with_gk) {
+      off = base;
+      const int gs = take(sizeof(double) * KWPB * (size_t)L.rw);
+      const int vo = take((size_t)vbytes * ent);
+      const int co = take(sizeof(int) * ent);
+      const int gk = with_gk ? take(sizeof(int) * KWPB * (size_t)L.rw) : -1;
+      if (off <= SMEM_LIMIT) {
+        L.resident = 1;
+        L.short_rows = max_row_len(P) <= 64;
+        L.gs_off = gs;
+        L.val_off = vo;
+        L.col_off = co;
+        L.gk_off = gk;
+        L.total = off;
+      }
     }
+    off = L.total;
   }
   return L;
 }
@@ -1963,6 +2118,8 @@ void apply_plan(KArgs &A, const SmemPlan &L) {
   A.rs_off = L.rs_off;
   A.cum_off = L.cum_off;
   A.col_off = L.col_off;
+  A.gk_off = L.gk_off >= 0 ? L.gk_off : 0;
+  A.flow = 0;  // the grid path turns it on (dataflow_setup)
 }
 
 // Cluster size and u slice (2^shift doubles per CTA) for a problem, or 0 when
@@ -2043,7 +2200,42 @@ int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int f32, int *shift) {
   return cs;
 }
 
-lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
+// Dataflow sweeps: for every CSR entry, the previous and the next entry of
+// its column in the sweep order (the CSC keeps each column's rows sorted by
+// sweep position), built once per problem.  A thread per column.
+__global__ void k_flow_deps(int n, const int *__restrict__ cp, const int *__restrict__ cpos, int *__restrict__ prev,
+                            int *__restrict__ next) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int q0 = cp[j], q1 = cp[j + 1];
+  for (int q = q0; q < q1; ++q) {
+    const int k = cpos[q];
+    prev[k] = q > q0 ? cpos[q - 1] : -1;
+    next[k] = q + 1 < q1 ? cpos[q + 1] : -1;
+  }
+}
+
+lpk_status ensure_flow(lpk_ctx *ctx, DevProblem &P) {
+  if (P.fl_flag) return LPK_OK;
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_prev, P.nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_next, P.nnz));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_flag, P.nnz));
+  if (P.n > 0) LPK_LAUNCH(ctx, k_flow_deps, (P.n + 255) / 256, 256, 0, ctx->stream, P.n, P.cp, P.cpos, P.fl_prev, P.fl_next);
+  LPK_CUDA_TRY(ctx, cudaGetLastError());
+  return LPK_OK;
+}
+
+// dataflow sweeps on the grid path: forced on or off by lpk_set_exec, else
+// for problems of 32 colors or more (where a grid barrier per color costs
+// more than the rows' waits)
+constexpr int FLOW_MIN_COLORS = 32;
+bool flow_wanted(const lpk_ctx *ctx, const DevProblem &P) {
+  if (ctx->flow_mode == 1) return false;
+  if (ctx->flow_mode == 2) return true;
+  return P.n_colors >= FLOW_MIN_COLORS;
+}
+
+lpk_status launch(lpk_ctx *ctx, DevProblem &P, KArgs &A, int f32) {
   if (!ctx->ev0) {
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
@@ -2104,7 +2296,8 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   size_t gsmem = 0;
   if (use_cs == 0) {
     gfn = kernel_for<GridGrp>(A.method, f32);
-    const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0);
+    const bool want_flow = flow_wanted(ctx, P);
+    const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0, want_flow);
     gsmem = L.total;
     if (gsmem > SMEM_LIMIT) {
       ctx->err = "too many colors for the shared-memory sweep state";
@@ -2120,9 +2313,18 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
     apply_plan(A, L);
     A.u_shift = 0;
     A.u_global = 0;
+    if (want_flow && L.resident && L.gk_off >= 0) {
+      const lpk_status fs = ensure_flow(ctx, P);
+      if (fs != LPK_OK) return fs;
+      A.flow = 1;
+      A.fl_prev = P.fl_prev;
+      A.fl_next = P.fl_next;
+      A.fl_flag = P.fl_flag;
+    }
   }
   ctx->last_resident = A.resident;
   ctx->last_u_global = A.u_global;
+  ctx->last_flow = A.flow;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->kctl, 0, sizeof(KrylovCtl), ctx->stream));
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   LPK_COUNT(ctx);
@@ -2150,7 +2352,8 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   for (int k = 0; k < 4; ++k) ctx->stats.phase_ms[k] += 1e-6 * (double)h->phase_ns[k];
   ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
-    ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
+    ctx->err = A.flow ? "a grid barrier or row-flag wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)"
+                      : "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
     return LPK_TIMEOUT;
   }
   return LPK_OK;
@@ -2160,7 +2363,7 @@ lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
 // problem's first solve (its actual matrix and right-hand side) and keep the
 // fastest for the problem.  Candidates: grid, clusters of 16, 8 and 4 CTAs
 // (each with the shared-memory row cache when it fits).
-lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
+lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32, int *probes) {
   // candidates: the grid; clusters of 16, 8 and 4 CTAs with u in shared
   // memory (u_place 1) or in global memory (u_place 2)
   const int cands[7][3] = {{1, 0, 0}, {2, 16, 1}, {2, 16, 2}, {2, 8, 1}, {2, 8, 2}, {2, 4, 1}, {2, 4, 2}};
@@ -2178,6 +2381,7 @@ lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
     A.max_restarts = 0;
     const double ms0 = ctx->stats.krylov_ms;
     const lpk_status st = launch(ctx, P, A, f32);
+    ++*probes;
     P.tuned_us[i] = 0.0;
     if (st == LPK_TIMEOUT) {
       ctx->cluster_mode = save_mode;
@@ -2207,6 +2411,81 @@ lpk_status autotune(lpk_ctx *ctx, DevProblem &P, const KArgs &base, int f32) {
   return LPK_OK;
 }
 
+// ---- tuning cache ------------------------------------------------------------
+// The autotuner's choice for a problem shape (rows, columns, nonzeros, colors,
+// longest row, Krylov method, value precision, SM count), kept for the
+// process and, when LPK_TUNE_CACHE names a file, appended to it and read back
+// by later processes: problems of a known shape skip the timing probes.  One
+// line per entry: "lpk-tune m n nnz colors maxrow method f32 sms mode cs ug".
+struct TuneEntry {
+  long long key[8];
+  int mode, cs, ug;
+};
+std::mutex g_tune_mu;
+std::vector<TuneEntry> g_tune;
+std::vector<std::string> g_tune_loaded;  // cache files already read
+
+void tune_key(lpk_ctx *ctx, const DevProblem &P, int method, int f32, long long (&k)[8]) {
+  k[0] = P.m;
+  k[1] = P.n;
+  k[2] = P.nnz;
+  k[3] = P.n_colors;
+  k[4] = max_row_len(P);
+  k[5] = method;
+  k[6] = f32;
+  k[7] = ctx->num_sms;
+}
+
+// with g_tune_mu held
+void tune_load(const std::string &path) {
+  for (const std::string &p : g_tune_loaded)
+    if (p == path) return;
+  g_tune_loaded.push_back(path);
+  FILE *f = std::fopen(path.c_str(), "r");
+  if (!f) return;
+  char tag[16];
+  TuneEntry e;
+  while (std::fscanf(f, "%15s %lld %lld %lld %lld %lld %lld %lld %lld %d %d %d", tag, &e.key[0], &e.key[1],
+                     &e.key[2], &e.key[3], &e.key[4], &e.key[5], &e.key[6], &e.key[7], &e.mode, &e.cs,
+                     &e.ug) == 12) {
+    if (std::string(tag) == "lpk-tune" && (e.mode == 1 || e.mode == 2) && e.cs >= 0 && e.cs <= MAX_CLUSTER)
+      g_tune.push_back(e);
+  }
+  std::fclose(f);
+}
+
+bool tune_lookup(const long long (&k)[8], TuneEntry *out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const char *path = std::getenv("LPK_TUNE_CACHE");
+  if (path && *path) tune_load(path);
+  for (const TuneEntry &e : g_tune) {
+    bool eq = true;
+    for (int i = 0; i < 8; ++i) eq = eq && e.key[i] == k[i];
+    if (eq) {
+      *out = e;
+      return true;
+    }
+  }
+  return false;
+}
+
+void tune_store(const long long (&k)[8], int mode, int cs, int ug) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneEntry e;
+  for (int i = 0; i < 8; ++i) e.key[i] = k[i];
+  e.mode = mode;
+  e.cs = cs;
+  e.ug = ug;
+  g_tune.push_back(e);
+  const char *path = std::getenv("LPK_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "lpk-tune %lld %lld %lld %lld %lld %lld %lld %lld %d %d %d\n", k[0], k[1], k[2], k[3], k[4], k[5],
+               k[6], k[7], mode, cs, ug);
+  std::fclose(f);
+}
+
 KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega) {
   KArgs A{};
   A.m = P.m;
@@ -2229,7 +2508,8 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.part = ctx->kpart;
   A.ctl = (KrylovCtl *)ctx->kctl;
   A.timeout_ns = ctx->wait_limit_ns;
-  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
+  A.stall_barrier = ctx->stall_barrier > 0 ? (unsigned long long)ctx->stall_barrier : 0ull;
+  A.stall_pass = ctx->stall_barrier < 0 ? (int)-ctx->stall_barrier : 0;
   A.prof = ctx->phase_timing;
   return A;
 }
@@ -2263,7 +2543,23 @@ lpk_status krylov_run(lpk_ctx *ctx, DevProblem &P, int kmethod, int precision, i
   A.dy = dy_hat;
   A.hist = hist;
   if (ctx->cluster_mode == 0 && !P.tuned && P.m > 0) {
-    if ((st = autotune(ctx, P, A, precision == LPK_MIXED)) != LPK_OK) return st;
+    const int f32 = precision == LPK_MIXED;
+    long long key[8];
+    tune_key(ctx, P, kmethod, f32, key);
+    TuneEntry e;
+    if (tune_lookup(key, &e)) {
+      P.tuned = 1;
+      P.tuned_mode = e.mode;
+      P.tuned_cs = e.cs;
+      P.tuned_ug = e.ug;
+      ctx->stats.tune_cache_hits++;
+    } else {
+      int probes = 0;
+      st = autotune(ctx, P, A, f32, &probes);
+      ctx->stats.tune_probes += probes;
+      if (st != LPK_OK) return st;
+      tune_store(key, P.tuned_mode, P.tuned_cs, P.tuned_ug);
+    }
   }
   st = launch(ctx, P, A, precision == LPK_MIXED);
   if (st != LPK_OK) return st;
@@ -2377,7 +2673,8 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   A.part = part;
   A.ctl = ctl;
   A.timeout_ns = ctx->wait_limit_ns;
-  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
+  A.stall_barrier = ctx->stall_barrier > 0 ? (unsigned long long)ctx->stall_barrier : 0ull;
+  A.stall_pass = ctx->stall_barrier < 0 ? (int)-ctx->stall_barrier : 0;
   A.f = f_hat;
   A.tol = tol;
   A.maxit = maxit;

@@ -49,6 +49,16 @@ struct DevProblem {
   double *aht = nullptr;         // [nnz] A_hat in CSC order (bitwise equal to ah64)
   int *cpos = nullptr;           // [nnz] CSR position of each CSC entry
 
+  // entry-balanced sparse products: chunks of SEG_CH entries; the first row
+  // (column) starting at or after each chunk, and one partial sum per chunk
+  int *seg_r = nullptr;          // [seg_chunks(nnz) + 1]
+  int *seg_c = nullptr;          // [seg_chunks(nnz) + 1]
+  double *seg_carry = nullptr;   // [seg_chunks(nnz)]
+
+  // dataflow sweeps (allocated on first use): per CSR entry, the previous and
+  // next entry of its column in the sweep order (-1: none), and its flag
+  int *fl_prev = nullptr, *fl_next = nullptr, *fl_flag = nullptr;
+
   int *color_ptr = nullptr;      // [n_colors+1] device copy
   std::vector<int> color_ptr_h;  // host copy
   std::vector<int> rp_h;         // host copy of rp (sizes the shared-memory row cache)
@@ -105,6 +115,8 @@ struct lpk_ctx {
   int last_resident = 0;         // the last launch cached the rows
   int u_place = 0;               // cluster path: 0 by the problem, 1 u in shared memory, 2 in global memory
   int last_u_global = 0;         // the last cluster launch kept u in global memory
+  int flow_mode = 0;             // grid path sweeps: 0 dataflow from 32 colors, 1 barriers, 2 dataflow
+  int last_flow = 0;             // the last grid launch ordered its sweeps by row flags
   unsigned long long wait_limit_ns = 5000000000ull;  // bound of every grid-barrier wait
   long long stall_barrier = 0;   // testing: grid barrier CTA 0 does not arrive at (0: none)
   int phase_timing = 0;          // persistent kernel: time its barrier intervals by phase kind
@@ -198,6 +210,12 @@ void free_problem(DevProblem &P);
 lpk_status ensure_reduce(lpk_ctx *ctx);
 
 // elementwise / sparse kernels (ipm_kernels.cu)
+constexpr int SEG_K = 8;              // entries per lane of the sparse products
+constexpr int SEG_CH = 32 * SEG_K;    // entries per warp (chunk)
+inline int seg_chunks(long long nnz) { return (int)((nnz + SEG_CH - 1) / SEG_CH); }
+// first[w] = first of the `rows` compressed rows starting at or after entry
+// w SEG_CH (w < seg_chunks(nnz)), first[seg_chunks(nnz)] = rows
+void seg_index(lpk_ctx *ctx, int rows, const int *rp, long long nnz, int *first);
 void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2);
 void spmv_csr(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y, const double *add,
               double sign);

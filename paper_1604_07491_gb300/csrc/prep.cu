@@ -305,7 +305,8 @@ void free_problem(DevProblem &P) {
   void *ptrs[] = {P.pos_of_in_row, P.in_row_of_pos, P.col_of_in, P.in_col_of, P.color_in, P.rp,
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
-                  P.gm_V,          P.ipm_buf,       P.dcol,      P.cpos};
+                  P.gm_V,          P.ipm_buf,       P.dcol,      P.cpos,      P.seg_r,     P.seg_c,
+                  P.seg_carry,     P.fl_prev,       P.fl_next,   P.fl_flag};
   for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }
@@ -498,6 +499,12 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.cpos, nnz));
   if (mr > 0) LPK_LAUNCH(ctx, k_csc_fill, nblk(mr), TPB, 0, st, mr, P.rp, P.ci, P.a, cursor, P.ri, P.at, P.cpos);
   if (nr > 0) LPK_LAUNCH(ctx, k_csc_sort, nblk(nr), TPB, 0, st, nr, P.cp, P.ri, P.at, P.cpos);
+  // ---- chunk index of the entry-balanced products ----------------------------
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_r, seg_chunks(nnz) + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_c, seg_chunks(nnz) + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_carry, seg_chunks(nnz)));
+  seg_index(ctx, mr, P.rp, nnz, P.seg_r);
+  seg_index(ctx, nr, P.cp, nnz, P.seg_c);
   // ---- maps to the input numbering ------------------------------------------
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.pos_of_in_row, m));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.color_in, m));
