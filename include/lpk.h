@@ -172,7 +172,7 @@ typedef struct lpk_stats {
                                  [3] the w-space image A_hat^T z */
   int32_t last_u_global;      /* 1: the last cluster launch kept u in global memory */
   int32_t last_dataflow;      /* 1: the last grid launch ordered its sweep rows by
-                                 per-entry flags instead of a barrier per color */
+                                 per-row flags instead of a barrier per color */
   int64_t tune_probes;        /* timing probes the autotuner launched */
   int64_t tune_cache_hits;    /* problems whose path came from the tuning cache */
 } lpk_stats;
@@ -205,17 +205,18 @@ typedef struct lpk_stats {
  * vector u lives in the CTAs' shared memory or in global memory (L2): by
  * default in global memory when a color carries 512 or more entries per CTA
  * (the autotuner, in LPK_EXEC_AUTO, times both); or-ing LPK_EXEC_U_SHARED or
- * LPK_EXEC_U_GLOBAL fixes the choice.  On the grid path with the row cache,
- * the sweeps of problems with 32 colors or more run in dataflow order: rows
- * of one color share no column, so instead of a grid barrier after every
- * color each row waits only for the rows before it that touch its columns
- * (a flag per nonzero, released after the row's update of u and acquired
- * before the next row reads u there; one barrier per pass).  Every row reads
- * the same u values either way, so results are bitwise those of the barrier
- * order.  Or-ing LPK_EXEC_COLOR_BARRIERS or LPK_EXEC_DATAFLOW fixes the
- * choice (dataflow needs the row cache; without it the barriers are used).
- * The dataflow order costs three ints per nonzero of device memory, taken on
- * the problem's first dataflow launch and kept until lpk_free_problem.
+ * LPK_EXEC_U_GLOBAL fixes the choice.  Or-ing LPK_EXEC_DATAFLOW runs the
+ * grid path's sweeps over cached rows in dataflow order: rows of one color
+ * share no column, so instead of a grid barrier after every color each warp
+ * waits only for the rows before it that touch its rows' columns (a flag per
+ * row, set after the row's update of u and polled before the next row reads
+ * u there; one barrier per pass).  Every row reads the same u values either
+ * way, so results are bitwise those of the barrier order.  It is off by
+ * default (LPK_EXEC_COLOR_BARRIERS, the default, states it): on this GPU the
+ * per-row waits and fences cost more than the barriers they replace.  The
+ * dataflow order takes two ints per nonzero and one per row of device
+ * memory on the problem's first dataflow launch, kept until
+ * lpk_free_problem; without the row cache the barriers are used.
  * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
 typedef enum lpk_exec {
   LPK_EXEC_AUTO = 0,

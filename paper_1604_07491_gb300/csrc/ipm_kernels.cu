@@ -139,44 +139,12 @@ __global__ void __launch_bounds__(TPB) k_seg_spmv(int rows, long long nnz, const
   double *lv = s_val[wib];
   const long long e0 = (long long)w * CH;
   const int len = (int)(nnz - e0 < CH ? nnz - e0 : CH);
-  const int ra = __ldg(first + w), rb = __ldg(first + w + 1);
-  // the row holding entry e0 began in an earlier chunk
-  const bool cont = ra >= rows || __ldg(rp + ra) > e0;
-  const int head_row = cont ? ra - 1 : -1;
-#pragma unroll
-  for (int j = 0; j < K; ++j) st[j * 32 + lane] = -1;
-  __syncwarp();
-  for (int r = ra + lane; r < rb; r += 32) {
-    const int p = __ldg(rp + r);
-    if (__ldg(rp + r + 1) > p) {
-      const int q = (int)(p - e0);
-      st[(q % K) * 32 + q / K] = r;
-    } else {
-      y[r] = seg_out(0.0, add, r, sign);  // empty row
-    }
-  }
-  __syncwarp();
-
   const int q0 = lane * K;
   const int nv = len - q0 < 0 ? 0 : (len - q0 < K ? len - q0 : K);  // entries of this lane
-  int mark[K];
-  int last = -1;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    mark[j] = st[j * 32 + lane];
-    last = max(last, mark[j]);
-  }
-  // the lane's incoming row: the latest start before its first entry
-  // (rows grow with the entry index, so a max-scan over the lanes)
-  int inc = last;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(FULL, inc, o);
-    if (lane >= o) inc = max(inc, v);
-  }
-  int incoming = __shfl_up_sync(FULL, inc, 1);
-  if (lane == 0 || incoming < 0) incoming = head_row;
-
+  // the loads are issued in dependency order so that their round trips
+  // overlap: chunk index, entries (index, value), row pointers, then the
+  // gathers of x
+  const int ra = __ldg(first + w), rb = __ldg(first + w + 1);
   int cv[K];
   double av[K], xv[K];
   const long long p0 = e0 + q0;
@@ -204,6 +172,41 @@ __global__ void __launch_bounds__(TPB) k_seg_spmv(int rows, long long nnz, const
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) xv[j] = j < nv ? __ldg(x + cv[j]) : 0.0;
+#pragma unroll
+  for (int j = 0; j < K; ++j) st[j * 32 + lane] = -1;
+  __syncwarp();
+  // rows starting in this chunk: mark their first entries
+  for (int r = ra + lane; r < rb; r += 32) {
+    const int p = __ldg(rp + r);
+    if (__ldg(rp + r + 1) > p) {
+      const int q = (int)(p - e0);
+      st[(q % K) * 32 + q / K] = r;
+    } else {
+      y[r] = seg_out(0.0, add, r, sign);  // empty row
+    }
+  }
+  // the row holding entry e0 began in an earlier chunk
+  const bool cont = ra >= rows || __ldg(rp + ra) > e0;
+  const int head_row = cont ? ra - 1 : -1;
+  __syncwarp();
+
+  int mark[K];
+  int last = -1;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    mark[j] = st[j * 32 + lane];
+    last = max(last, mark[j]);
+  }
+  // the lane's incoming row: the latest start before its first entry
+  // (rows grow with the entry index, so a max-scan over the lanes)
+  int inc = last;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc = max(inc, v);
+  }
+  int incoming = __shfl_up_sync(FULL, inc, 1);
+  if (lane == 0 || incoming < 0) incoming = head_row;
 
   // the lane's entries in order: a start ends the current row's run
   int cur = incoming, nst = 0, cnt = 0;

@@ -1,7 +1,7 @@
-"""Dataflow sweeps (grid path, rows cached in shared memory): instead of a
-grid barrier after every color, each row waits on per-nonzero flags of the
-rows before it that touch its columns (the previous entry of each of its
-columns in the sweep order), and one barrier ends each pass.  Rows of one
+"""Dataflow sweeps (grid path, rows cached in shared memory; LPK_EXEC_DATAFLOW):
+instead of a grid barrier after every color, each warp waits on the flags of
+the rows before its rows that touch their columns (the previous row of each
+column in the sweep order), and one barrier ends each pass.  Rows of one
 color share no column, so every row reads exactly the u values it reads with
 a barrier per color: the results must be bitwise those of the per-color
 barrier order.  Checked for lone sweeps (NE-SOR and NE-SSOR, several inner
