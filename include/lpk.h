@@ -171,8 +171,7 @@ typedef struct lpk_stats {
                                  (with the product w = A_hat z before it),
                                  [3] the w-space image A_hat^T z */
   int32_t last_u_global;      /* 1: the last cluster launch kept u in global memory */
-  int32_t last_dataflow;      /* 1: the last grid launch ordered its sweep rows by
-                                 per-row flags instead of a barrier per color */
+  int32_t reserved;
   int64_t tune_probes;        /* timing probes the autotuner launched */
   int64_t tune_cache_hits;    /* problems whose path came from the tuning cache */
 } lpk_stats;
@@ -205,18 +204,7 @@ typedef struct lpk_stats {
  * vector u lives in the CTAs' shared memory or in global memory (L2): by
  * default in global memory when a color carries 512 or more entries per CTA
  * (the autotuner, in LPK_EXEC_AUTO, times both); or-ing LPK_EXEC_U_SHARED or
- * LPK_EXEC_U_GLOBAL fixes the choice.  Or-ing LPK_EXEC_DATAFLOW runs the
- * grid path's sweeps over cached rows in dataflow order: rows of one color
- * share no column, so instead of a grid barrier after every color each warp
- * waits only for the rows before it that touch its rows' columns (a flag per
- * row, set after the row's update of u and polled before the next row reads
- * u there; one barrier per pass).  Every row reads the same u values either
- * way, so results are bitwise those of the barrier order.  It is off by
- * default (LPK_EXEC_COLOR_BARRIERS, the default, states it): on this GPU the
- * per-row waits and fences cost more than the barriers they replace.  The
- * dataflow order takes two ints per nonzero and one per row of device
- * memory on the problem's first dataflow launch, kept until
- * lpk_free_problem; without the row cache the barriers are used.
+ * LPK_EXEC_U_GLOBAL fixes the choice.
  * cluster_size: 0 = chosen from nnz, else 2, 4, 8 or 16 CTAs. */
 typedef enum lpk_exec {
   LPK_EXEC_AUTO = 0,
@@ -225,9 +213,7 @@ typedef enum lpk_exec {
   LPK_EXEC_BATCH = 3,
   LPK_EXEC_NO_RESIDENT = 4,
   LPK_EXEC_U_SHARED = 8,
-  LPK_EXEC_U_GLOBAL = 16,
-  LPK_EXEC_COLOR_BARRIERS = 32,
-  LPK_EXEC_DATAFLOW = 64
+  LPK_EXEC_U_GLOBAL = 16
 } lpk_exec;
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream` (a
@@ -242,18 +228,14 @@ LPK_API lpk_status lpk_reset_stats(lpk_ctx *ctx);
 LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size);
 
 /* Failure detection of the grid path (the paper has no counterpart).  Every
- * wait of the persistent kernel's software grid barrier, and every row-flag
- * wait of the dataflow sweeps, is bounded by `seconds` of %globaltimer
- * (default 5; must be > 0): when it runs out, the thread records
- * LPK_TIMEOUT, every CTA leaves the kernel at its next barrier (a row-flag
- * wait gives up as soon as the status is set), and the call returns
- * LPK_TIMEOUT with the context still usable.
- * test_stall_barrier (testing only, 0 = off): k > 0: in each grid-path
- * launch, CTA 0 withholds its arrival at the grid barrier with number k
- * (counted from 1 in the launch); k < 0: in dataflow sweeps, CTA 0 publishes
- * no row flag from sweep pass -k (counted from 1 in the launch) on.  Every
- * wait on the withheld arrival or flags runs out; this is how the timeout
- * paths are exercised without faulting the GPU.  The cluster path's hardware
+ * wait of the persistent kernel's software grid barrier is bounded by
+ * `seconds` of %globaltimer (default 5; must be > 0): when it runs out, the
+ * CTA records LPK_TIMEOUT, every CTA leaves the kernel at its next barrier,
+ * and the call returns LPK_TIMEOUT with the context still usable.
+ * test_stall_barrier (testing only, 0 = off): in each grid-path launch, CTA 0
+ * withholds its arrival at the grid barrier with that number (counted from 1
+ * in the launch), so every wait on it runs out; this is how the timeout path
+ * is exercised without faulting the GPU.  The cluster path's hardware
  * barriers have no software wait and are not affected. */
 LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier);
 

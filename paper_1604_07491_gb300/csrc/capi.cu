@@ -151,7 +151,6 @@ LPK_API lpk_status lpk_get_stats(const lpk_ctx *ctx, lpk_stats *out) {
   out->last_cluster_size = ctx->last_cluster;
   out->last_resident = ctx->last_resident;
   out->last_u_global = ctx->last_u_global;
-  out->last_dataflow = ctx->last_flow;
   return LPK_OK;
 }
 
@@ -159,16 +158,13 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
   if (!ctx) return LPK_INVALID_ARG;
   const int no_res = (exec & LPK_EXEC_NO_RESIDENT) != 0;
   const int ush = (exec & LPK_EXEC_U_SHARED) != 0, ugl = (exec & LPK_EXEC_U_GLOBAL) != 0;
-  const int cbar = (exec & LPK_EXEC_COLOR_BARRIERS) != 0, dflow = (exec & LPK_EXEC_DATAFLOW) != 0;
-  exec &= ~(LPK_EXEC_NO_RESIDENT | LPK_EXEC_U_SHARED | LPK_EXEC_U_GLOBAL | LPK_EXEC_COLOR_BARRIERS |
-            LPK_EXEC_DATAFLOW);
-  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_BATCH || (ush && ugl) || (cbar && dflow) ||
+  exec &= ~(LPK_EXEC_NO_RESIDENT | LPK_EXEC_U_SHARED | LPK_EXEC_U_GLOBAL);
+  if (exec < LPK_EXEC_AUTO || exec > LPK_EXEC_BATCH || (ush && ugl) ||
       !(cluster_size == 0 || cluster_size == 2 || cluster_size == 4 || cluster_size == 8 || cluster_size == 16)) {
-    ctx->err = "lpk_set_exec: exec must be 0..3 (with at most one of U_SHARED, U_GLOBAL and at most one of "
-               "COLOR_BARRIERS, DATAFLOW) and cluster_size 0, 2, 4, 8 or 16";
+    ctx->err = "lpk_set_exec: exec must be 0..3 (with at most one of U_SHARED, U_GLOBAL) and cluster_size 0, 2, 4, 8 "
+               "or 16";
     return LPK_INVALID_ARG;
   }
-  ctx->flow_mode = cbar ? 1 : dflow ? 2 : 0;
   ctx->cluster_mode = exec;
   ctx->cluster_size_override = cluster_size;
   ctx->resident_mode = no_res;
@@ -178,8 +174,8 @@ LPK_API lpk_status lpk_set_exec(lpk_ctx *ctx, int32_t exec, int32_t cluster_size
 
 LPK_API lpk_status lpk_set_wait_limit(lpk_ctx *ctx, double seconds, int64_t test_stall_barrier) {
   if (!ctx) return LPK_INVALID_ARG;
-  if (!(seconds > 0.0 && seconds < 1e6) || test_stall_barrier < -((int64_t)1 << 30)) {
-    ctx->err = "lpk_set_wait_limit: seconds must be in (0, 1e6) and test_stall_barrier >= -2^30";
+  if (!(seconds > 0.0 && seconds < 1e6) || test_stall_barrier < 0) {
+    ctx->err = "lpk_set_wait_limit: seconds must be in (0, 1e6) and test_stall_barrier >= 0";
     return LPK_INVALID_ARG;
   }
   ctx->wait_limit_ns = (unsigned long long)(seconds * 1e9);

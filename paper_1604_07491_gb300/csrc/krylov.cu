@@ -100,11 +100,6 @@ struct KArgs {
   int prof;                        // phase timing: CTA 0 charges each barrier interval to its phase kind
   unsigned long long timeout_ns;   // grid path: bound of every barrier wait
   unsigned long long stall_barrier;  // grid path, testing: barrier CTA 0 does not arrive at (0: none)
-  int stall_pass;                  // dataflow sweeps, testing: pass from which CTA 0 publishes no flag (0: none)
-  int flow;                        // grid path, rows cached: dataflow sweeps (see Flow)
-  const int *fl_prev, *fl_next;    // per CSR entry: the row of the previous / next entry of its column (-1: none)
-  int *fl_flag;                    // per row (sweep position): last pass written
-  int gk_off;                      // shared-memory offset of the slots' first CSR entries
   double *dw, *dy;                 // outputs (n), (m)
   double *g, *t, *qt, *pt, *by;    // m-space workspace
   double *q, *p0, *p1, *bw;        // n-space workspace
@@ -135,77 +130,6 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-
-// ---- dataflow order of the sweep rows (grid path, rows cached) ------------
-// Rows of one color share no column, so a row needs only the rows before it
-// in the sweep order that touch its columns -- for each of its entries, the
-// previous row of the same column (the column's last writer).  Instead of a
-// grid barrier after every color, a warp polls those rows' flags before it
-// reads u at the row's columns and sets its rows' flags after it has written
-// u there.  Every row then reads exactly the u values it reads with a barrier
-// per color: the result is bitwise the same.  A pass is numbered from 1
-// within the launch; flag[p] = the last pass in which the row at sweep
-// position p is written (zeroed when the launch starts).
-//
-// Ordering: the polls are relaxed loads issued together (one round trip for
-// all of a lane's entries), followed by a fence (acquire) before the u loads;
-// after a warp's u stores every lane fences, the warp synchronises, and one
-// lane per row stores the row's flag with release semantics.
-__device__ __forceinline__ int ld_relaxed_i32(const int *p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_i32(int *p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-struct Flow {
-  const int *dep;    // per CSR entry: the row (sweep position) it follows in this pass (-1: none); null: barriers
-  int *flag;         // per row (sweep position)
-  const int *gk;     // this warp's slots: the row's first CSR entry
-  const int *rows;   // this warp's slots: the row's sweep position
-  int pass;
-  int withhold;      // testing: this CTA sets no flag (every wait on it runs out)
-  int *status;
-  unsigned long long timeout_ns;
-};
-
-// wait until the rows d[i] (-1: none) are written in this pass.  Bounded by
-// timeout_ns (then the launch's status becomes LPK_TIMEOUT) and given up once
-// another wait has failed; every lane of the warp calls it.
-template <int N>
-__device__ __forceinline__ void flow_wait(const Flow &F, const int (&d)[N]) {
-  unsigned it = 0;
-  unsigned long long t0 = 0;
-  for (;;) {
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      if (d[i] >= 0 && ld_relaxed_i32(F.flag + d[i]) < F.pass) ok = false;
-    if (ok) break;
-    if ((++it & 31u) == 0u) {
-      if (*(volatile int *)F.status != 0) break;
-      const unsigned long long now = globaltimer();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > F.timeout_ns) {
-        atomicCAS(F.status, 0, (int)LPK_TIMEOUT);
-        break;
-      }
-    }
-  }
-  fence_acq_rel_gpu();  // acquire: the u loads that follow see the flagged rows' stores
-}
-
-// publish the warp's rows of slots [s0, s0 + nb) after their u stores
-__device__ __forceinline__ void flow_post(const Flow &F, int s0, int nb) {
-  const int lane = threadIdx.x & 31;
-  fence_acq_rel_gpu();
-  __syncwarp();
-  if (lane < nb && !F.withhold) st_release_i32(F.flag + F.rows[s0 + lane], F.pass);
 }
 
 // ---- double-word (FP32 pair) arithmetic of the mixed-precision sweeps ------
@@ -461,7 +385,6 @@ struct ZStore {
   int *cum;      // [KWPB][nc + 1]
   void *vals;    // [entries of the CTA]   resident only (TV)
   int *cols;     // [entries of the CTA]   resident only
-  int *gk;       // [KWPB][rw]   dataflow only: first CSR entry of the slot's row
   int rw, nc;
   __device__ __forceinline__ int wi() const { return threadIdx.x >> 5; }
   __device__ __forceinline__ double *zw() const { return zs + wi() * rw; }
@@ -469,7 +392,6 @@ struct ZStore {
   __device__ __forceinline__ const int2 *dw() const { return desc + wi() * rw; }
   __device__ __forceinline__ const int *rw_rows() const { return rs + wi() * rw; }
   __device__ __forceinline__ const int *cw() const { return cum + wi() * (nc + 1); }
-  __device__ __forceinline__ const int *gkw() const { return gk + wi() * rw; }
 };
 
 __device__ __forceinline__ ZStore make_zstore(const KArgs &A) {
@@ -482,7 +404,6 @@ __device__ __forceinline__ ZStore make_zstore(const KArgs &A) {
   Z.cum = (int *)(dyn_smem_b + A.cum_off);
   Z.vals = (void *)(dyn_smem_b + A.val_off);
   Z.cols = (int *)(dyn_smem_b + A.col_off);
-  Z.gk = (int *)(dyn_smem_b + A.gk_off);
   Z.rw = A.rw;
   Z.nc = A.nc;
   return Z;
@@ -541,7 +462,6 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
   const TV *a = ahat<TV>(A);
   TV *vals = (TV *)Z.vals;
   int off = basew;
-  int *gkw = Z.gk + w * Z.rw;
   for (int sl = 0; sl < carry; ++sl) {
     const int2 kl = dw[sl];
     for (int t = lane; t < kl.y; t += 32) {
@@ -549,13 +469,7 @@ __device__ __forceinline__ void zstore_init(const KArgs &A, const ZStore &Z, int
       vals[off + t] = __ldg(a + kl.x + t);
     }
     __syncwarp();
-    if (lane == 0) {
-      if (A.flow) {
-        gkw[sl] = kl.x;
-        A.fl_flag[rsw[sl]] = 0;  // ordered before any wait by the barrier ahead of the first sweep
-      }
-      dw[sl] = make_int2(off, kl.y);
-    }
+    if (lane == 0) dw[sl] = make_int2(off, kl.y);
     off += kl.y;
   }
   __syncwarp();
@@ -618,12 +532,9 @@ __device__ __forceinline__ double row_update(const GRP &Gp, const KArgs &A, cons
 }
 
 // Row update from the shared-memory row cache (resident rows).
-// With F.dep (dataflow sweeps; sl = the row's slot): the warp waits for the
-// rows its entries follow before reading u and publishes the row after
-// writing u.
 template <typename TV, typename GRP>
 __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, const int *cols, int e0, int len,
-                                                 double g, double om, const Flow &F, int sl) {
+                                                 double g, double om) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
   if (len <= 32 * RCR) {
@@ -635,12 +546,6 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
         cv[e] = cols[e0 + lane + 32 * e];
         av[e] = (double)vals[e0 + lane + 32 * e];
       }
-    if (F.dep) {
-      int dd[RCR];
-#pragma unroll
-      for (int e = 0; e < RCR; ++e) dd[e] = lane + 32 * e < len ? __ldg(F.dep + F.gk[sl] + lane + 32 * e) : -1;
-      flow_wait(F, dd);
-    }
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) {
@@ -652,14 +557,7 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) Gp.ust(cv[e], uv[e] + d * av[e]);
-    if (F.dep) flow_post(F, sl, 1);
     return d;
-  }
-  if (F.dep) {
-    for (int t = lane; t < len; t += 32) {
-      const int dd[1] = {__ldg(F.dep + F.gk[sl] + t)};
-      flow_wait(F, dd);
-    }
   }
   for (int t = lane; t < len; t += 32) s += (double)vals[e0 + t] * Gp.uld(cols[e0 + t]);
   s = warp_sum(s);
@@ -668,7 +566,6 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
     const int c = cols[e0 + t];
     Gp.ust(c, Gp.uld(c) + d * (double)vals[e0 + t]);
   }
-  if (F.dep) flow_post(F, sl, 1);
   return d;
 }
 
@@ -682,7 +579,7 @@ __device__ __forceinline__ double row_update_res(const GRP &Gp, const TV *vals, 
 template <typename TV, typename GRP>
 __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, const int *cols, const int2 *dw,
                                                const double *gsw, double *zw, int s0, int s1, double om,
-                                               bool firstpass, bool lastpass, double *acc, const Flow &F) {
+                                               bool firstpass, bool lastpass, double *acc) {
   constexpr int NB = sizeof(TV) == 4 ? 4 : 2, E = 2;  // FP64 values need twice the registers
   const int lane = threadIdx.x & 31;
   for (int sb = s0; sb < s1; sb += NB) {
@@ -705,15 +602,6 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
     // rows of this batch (warp-uniform): FP64 work is spent on them only, an
     // FP64 warp instruction being costly on this GPU
     const int nb = min(NB, s1 - sb);
-    // dataflow: the rows of a batch share a color, so none waits on another
-    if (F.dep) {
-      int dd[NB * E];
-#pragma unroll
-      for (int k = 0; k < NB; ++k)
-#pragma unroll
-        for (int e = 0; e < E; ++e) dd[k * E + e] = cv[k][e] >= 0 ? __ldg(F.dep + F.gk[sb + k] + lane + 32 * e) : -1;
-      flow_wait(F, dd);
-    }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
 #pragma unroll
@@ -749,7 +637,6 @@ __device__ __forceinline__ void rows_res_short(const GRP &Gp, const TV *vals, co
         }
       }
     }
-    if (F.dep) flow_post(F, sb, nb);
   }
 }
 
@@ -797,8 +684,7 @@ __device__ __forceinline__ float2 row_update_dw(const GRP &Gp, const KArgs &A, c
 // one row from the shared-memory row cache
 template <typename GRP>
 __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *vals, const int *cols, int e0,
-                                                    int len, float2 g2, float2 om2, bool om1, const Flow &F,
-                                                    int sl) {
+                                                    int len, float2 g2, float2 om2, bool om1) {
   const int lane = threadIdx.x & 31;
   float2 s = make_float2(0.f, 0.f);
   if (len <= 32 * RCR) {
@@ -811,12 +697,6 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
         cv[e] = cols[e0 + lane + 32 * e];
         av[e] = vals[e0 + lane + 32 * e];
       }
-    if (F.dep) {
-      int dd[RCR];
-#pragma unroll
-      for (int e = 0; e < RCR; ++e) dd[e] = lane + 32 * e < len ? __ldg(F.dep + F.gk[sl] + lane + 32 * e) : -1;
-      flow_wait(F, dd);
-    }
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) uv[e] = Gp.uld2(cv[e]);
@@ -830,14 +710,7 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
 #pragma unroll
     for (int e = 0; e < RCR; ++e)
       if (lane + 32 * e < len) Gp.ust2(cv[e], dw_add(uv[e], dw_mulf(d, av[e])));
-    if (F.dep) flow_post(F, sl, 1);
     return d;
-  }
-  if (F.dep) {
-    for (int t = lane; t < len; t += 32) {
-      const int dd[1] = {__ldg(F.dep + F.gk[sl] + t)};
-      flow_wait(F, dd);
-    }
   }
   for (int t = lane; t < len; t += 32) s = dw_add(s, dw_mulf(Gp.uld2(cols[e0 + t]), vals[e0 + t]));
 #pragma unroll
@@ -848,7 +721,6 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
     const int c = cols[e0 + t];
     Gp.ust2(c, dw_add(Gp.uld2(c), dw_mulf(d, vals[e0 + t])));
   }
-  if (F.dep) flow_post(F, sl, 1);
   return d;
 }
 
@@ -857,7 +729,7 @@ __device__ __forceinline__ float2 row_update_res_dw(const GRP &Gp, const float *
 template <typename GRP>
 __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *vals, const int *cols,
                                                   const int2 *dw, const float2 *gs2, float2 *zw2, int s0, int s1,
-                                                  float2 om2, bool om1, bool firstpass, const Flow &F) {
+                                                  float2 om2, bool om1, bool firstpass) {
   constexpr int NB = 4, E = 2;
   const int lane = threadIdx.x & 31;
   for (int sb = s0; sb < s1; sb += NB) {
@@ -878,14 +750,6 @@ __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *va
           av[k][e] = vals[kl.x + t];
         }
       }
-    }
-    if (F.dep) {  // the rows of a batch share a color: none waits on another
-      int dd[NB * E];
-#pragma unroll
-      for (int k = 0; k < NB; ++k)
-#pragma unroll
-        for (int e = 0; e < E; ++e) dd[k * E + e] = cv[k][e] >= 0 ? __ldg(F.dep + F.gk[sb + k] + lane + 32 * e) : -1;
-      flow_wait(F, dd);
     }
 #pragma unroll
     for (int k = 0; k < NB; ++k)
@@ -918,15 +782,11 @@ __device__ __forceinline__ void rows_res_short_dw(const GRP &Gp, const float *va
         if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
       }
     }
-    if (F.dep) flow_post(F, sb, nb);
   }
 }
 
 // inner_sweeps with every row of the warp resident in shared memory: the only
 // global/distributed accesses of a color phase are the gather and scatter of u.
-// With A.flow (grid path) the colors of a pass are not separated by grid
-// barriers: rows wait on their entries' predecessors instead (see Flow), and
-// one barrier ends each pass.
 template <typename TV, typename GRP>
 __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const double *g, bool ssor, double *acc,
                                  Counters &C, const ZStore &Z) {
@@ -940,29 +800,6 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
   const TV *vals = (const TV *)Z.vals;
   const int *cols = Z.cols;
   const int nslots = cw[nc];
-  const long long pass0 = C.passes;
-  Flow F{nullptr, A.fl_flag, A.flow ? Z.gkw() : nullptr, rsw, 0, 0, &A.ctl->status, A.timeout_ns};
-  auto flow_pass = [&](int ps, bool backward) {
-    if (!A.flow) return;
-    F.dep = backward ? A.fl_next : A.fl_prev;
-    F.pass = (int)(pass0 + ps + 1);
-    F.withhold = A.stall_pass != 0 && blockIdx.x == 0 && F.pass >= A.stall_pass;
-  };
-  // a barrier between colors (per-color mode), or at the end of a pass
-  // (dataflow mode; none after the last pass, as in per-color mode)
-  auto color_end = [&](bool lastpass, int cc) -> bool {
-    if (A.flow ? (cc == nc - 1 && !lastpass) : !(lastpass && cc == nc - 1)) return Gp.sync(s_ok);
-    return true;
-  };
-  // dataflow: a failed wait sets the launch's status; every CTA reads it
-  // after the barrier that follows the sweep
-  auto flow_status = [&]() -> bool {
-    if (!A.flow) return true;
-    if (!Gp.sync(s_ok)) return false;
-    if (threadIdx.x == 0) *s_ok = *(volatile int *)&A.ctl->status == 0;
-    __syncthreads();
-    return *s_ok != 0;
-  };
   if constexpr (std::is_same<TV, float>::value) {
     // FP32 values: double-word rows; z and g slots hold double words, and the
     // (z, g) product of the last pass is formed when z is written out
@@ -975,23 +812,22 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
     for (int ps = 0; ps < passes; ++ps) {
       const bool backward = ssor && (ps & 1);
       const bool firstpass = ps == 0, lastpass = ps == passes - 1;
-      flow_pass(ps, backward);
       for (int cc = 0; cc < nc; ++cc) {
         const int c = backward ? nc - 1 - cc : cc;
         if (A.short_rows) {
-          rows_res_short_dw(Gp, vals, cols, dw, gs2, zw2, cw[c], cw[c + 1], om2, om1, firstpass, F);
+          rows_res_short_dw(Gp, vals, cols, dw, gs2, zw2, cw[c], cw[c + 1], om2, om1, firstpass);
         } else {
           for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
             const int2 kl = dw[sl];
-            const float2 d =
-                row_update_res_dw(Gp, vals, cols, kl.x, kl.y, gs2[sl], om2, om1, F, sl);
+            const float2 d = row_update_res_dw(Gp, vals, cols, kl.x, kl.y, gs2[sl], om2, om1);
             if (lane == 0) zw2[sl] = firstpass ? d : dw_add(zw2[sl], d);
           }
         }
-        if (!color_end(lastpass, cc)) return false;
+        if (!(lastpass && cc == nc - 1)) {
+          if (!Gp.sync(s_ok)) return false;
+        }
       }
     }
-    if (!flow_status()) return false;
     __syncwarp();
     for (int sl = lane; sl < nslots; sl += 32) {
       const double zr = dw_val(zw2[sl]);
@@ -1009,16 +845,15 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
   for (int ps = 0; ps < passes; ++ps) {
     const bool backward = ssor && (ps & 1);
     const bool firstpass = ps == 0, lastpass = ps == passes - 1;
-    flow_pass(ps, backward);
     for (int cc = 0; cc < nc; ++cc) {
       const int c = backward ? nc - 1 - cc : cc;
       if (A.short_rows) {
-        rows_res_short<TV>(Gp, vals, cols, dw, gsw, zw, cw[c], cw[c + 1], om, firstpass, lastpass, acc, F);
+        rows_res_short<TV>(Gp, vals, cols, dw, gsw, zw, cw[c], cw[c + 1], om, firstpass, lastpass, acc);
       } else {
         for (int sl = cw[c]; sl < cw[c + 1]; ++sl) {
           const int2 kl = dw[sl];
           const double gr = gsw[sl];
-          const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om, F, sl);
+          const double d = row_update_res<TV>(Gp, vals, cols, kl.x, kl.y, gr, om);
           if (lane == 0) {
             const double zn = firstpass ? d : zw[sl] + d;
             zw[sl] = zn;
@@ -1026,10 +861,11 @@ __device__ bool inner_sweeps_res(const KArgs &A, GRP &Gp, int *s_ok, const doubl
           }
         }
       }
-      if (!color_end(lastpass, cc)) return false;
+      if (!(lastpass && cc == nc - 1)) {
+        if (!Gp.sync(s_ok)) return false;
+      }
     }
   }
-  if (!flow_status()) return false;
   __syncwarp();
   for (int sl = lane; sl < nslots; sl += 32) A.z[rsw[sl]] = zw[sl];
   if (!acc) {
@@ -2067,7 +1903,6 @@ struct SmemPlan {
   size_t total = 0;
   int rw = 0, resident = 0, short_rows = 0;
   int z_off = 0, gs_off = 0, desc_off = 0, val_off = 0, rs_off = 0, cum_off = 0, col_off = 0;
-  int gk_off = -1;  // the slots' first CSR entries (dataflow sweeps), -1: none
 };
 
 // nonzeros of the busiest CTA when the rows are dealt round-robin by sweep
@@ -2087,8 +1922,7 @@ int max_row_len(const DevProblem &P) {
   return mx;
 }
 
-SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident,
-                   bool flow = false) {
+SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bool allow_resident) {
   SmemPlan L;
   const int GW = ctas * KWPB;
   L.rw = std::max(1, (P.m + GW - 1) / GW);  // rows per warp (round-robin by position)
@@ -2105,25 +1939,17 @@ SmemPlan plan_smem(const DevProblem &P, int ctas, size_t u_bytes, int vbytes, bo
   L.total = off;
   if (allow_resident && (long long)P.rp_h.size() == (long long)P.m + 1) {
     const long long ent = max_cta_entries(P, ctas);
-    const size_t base = off;
-    // with the dataflow block if asked for and it fits, else without
-    for (int with_gk = flow ? 1 : 0; with_gk >= 0 && !L.resident; --with_gk) {
-      off = base;
-      const int gs = take(sizeof(double) * KWPB * (size_t)L.rw);
-      const int vo = take((size_t)vbytes * ent);
-      const int co = take(sizeof(int) * ent);
-      const int gk = with_gk ? take(sizeof(int) * KWPB * (size_t)L.rw) : -1;
-      if (off <= SMEM_LIMIT) {
-        L.resident = 1;
-        L.short_rows = max_row_len(P) <= 64;
-        L.gs_off = gs;
-        L.val_off = vo;
-        L.col_off = co;
-        L.gk_off = gk;
-        L.total = off;
-      }
+    const int gs = take(sizeof(double) * KWPB * (size_t)L.rw);
+    const int vo = take((size_t)vbytes * ent);
+    const int co = take(sizeof(int) * ent);
+    if (off <= SMEM_LIMIT) {
+      L.resident = 1;
+      L.short_rows = max_row_len(P) <= 64;
+      L.gs_off = gs;
+      L.val_off = vo;
+      L.col_off = co;
+      L.total = off;
     }
-    off = L.total;
   }
   return L;
 }
@@ -2139,8 +1965,6 @@ void apply_plan(KArgs &A, const SmemPlan &L) {
   A.rs_off = L.rs_off;
   A.cum_off = L.cum_off;
   A.col_off = L.col_off;
-  A.gk_off = L.gk_off >= 0 ? L.gk_off : 0;
-  A.flow = 0;  // the grid path turns it on (dataflow_setup)
 }
 
 // Cluster size and u slice (2^shift doubles per CTA) for a problem, or 0 when
@@ -2221,40 +2045,7 @@ int cluster_plan(lpk_ctx *ctx, const DevProblem &P, int f32, int *shift) {
   return cs;
 }
 
-// Dataflow sweeps: for every CSR entry, the rows (sweep positions) of the
-// previous and the next entry of its column in the sweep order (the CSC
-// keeps each column's rows sorted by sweep position), built once per
-// problem.  A thread per column.
-__global__ void k_flow_deps(int n, const int *__restrict__ cp, const int *__restrict__ ri,
-                            const int *__restrict__ cpos, int *__restrict__ prev, int *__restrict__ next) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const int q0 = cp[j], q1 = cp[j + 1];
-  for (int q = q0; q < q1; ++q) {
-    const int k = cpos[q];
-    prev[k] = q > q0 ? ri[q - 1] : -1;
-    next[k] = q + 1 < q1 ? ri[q + 1] : -1;
-  }
-}
-
-lpk_status ensure_flow(lpk_ctx *ctx, DevProblem &P) {
-  if (P.fl_flag) return LPK_OK;
-  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_prev, P.nnz));
-  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_next, P.nnz));
-  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.fl_flag, P.m));
-  if (P.n > 0)
-    LPK_LAUNCH(ctx, k_flow_deps, (P.n + 255) / 256, 256, 0, ctx->stream, P.n, P.cp, P.ri, P.cpos, P.fl_prev, P.fl_next);
-  LPK_CUDA_TRY(ctx, cudaGetLastError());
-  return LPK_OK;
-}
-
-// dataflow sweeps on the grid path only when asked for (LPK_EXEC_DATAFLOW):
-// measured on the large LP (406 colors), a pass takes 3.6 ms in dataflow
-// order against 1.3 ms with a barrier per color -- each row's wait, fences
-// and flag hand-off cost more than its share of a barrier
-bool flow_wanted(const lpk_ctx *ctx, const DevProblem &) { return ctx->flow_mode == 2; }
-
-lpk_status launch(lpk_ctx *ctx, DevProblem &P, KArgs &A, int f32) {
+lpk_status launch(lpk_ctx *ctx, const DevProblem &P, KArgs &A, int f32) {
   if (!ctx->ev0) {
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev0));
     LPK_CUDA_TRY(ctx, cudaEventCreate(&ctx->ev1));
@@ -2315,8 +2106,7 @@ lpk_status launch(lpk_ctx *ctx, DevProblem &P, KArgs &A, int f32) {
   size_t gsmem = 0;
   if (use_cs == 0) {
     gfn = kernel_for<GridGrp>(A.method, f32);
-    const bool want_flow = flow_wanted(ctx, P);
-    const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0, want_flow);
+    const SmemPlan L = plan_smem(P, ctx->num_sms, 0, f32 ? 4 : 8, ctx->resident_mode == 0);
     gsmem = L.total;
     if (gsmem > SMEM_LIMIT) {
       ctx->err = "too many colors for the shared-memory sweep state";
@@ -2332,18 +2122,9 @@ lpk_status launch(lpk_ctx *ctx, DevProblem &P, KArgs &A, int f32) {
     apply_plan(A, L);
     A.u_shift = 0;
     A.u_global = 0;
-    if (want_flow && L.resident && L.gk_off >= 0) {
-      const lpk_status fs = ensure_flow(ctx, P);
-      if (fs != LPK_OK) return fs;
-      A.flow = 1;
-      A.fl_prev = P.fl_prev;
-      A.fl_next = P.fl_next;
-      A.fl_flag = P.fl_flag;
-    }
   }
   ctx->last_resident = A.resident;
   ctx->last_u_global = A.u_global;
-  ctx->last_flow = A.flow;
   LPK_CUDA_TRY(ctx, cudaMemsetAsync(ctx->kctl, 0, sizeof(KrylovCtl), ctx->stream));
   LPK_CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   LPK_COUNT(ctx);
@@ -2371,8 +2152,7 @@ lpk_status launch(lpk_ctx *ctx, DevProblem &P, KArgs &A, int f32) {
   for (int k = 0; k < 4; ++k) ctx->stats.phase_ms[k] += 1e-6 * (double)h->phase_ns[k];
   ctx->last_cluster = use_cs;
   if (h->status == LPK_TIMEOUT) {
-    ctx->err = A.flow ? "a grid barrier or row-flag wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)"
-                      : "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
+    ctx->err = "a grid barrier wait of the persistent Krylov kernel timed out (lpk_set_wait_limit)";
     return LPK_TIMEOUT;
   }
   return LPK_OK;
@@ -2527,8 +2307,7 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.part = ctx->kpart;
   A.ctl = (KrylovCtl *)ctx->kctl;
   A.timeout_ns = ctx->wait_limit_ns;
-  A.stall_barrier = ctx->stall_barrier > 0 ? (unsigned long long)ctx->stall_barrier : 0ull;
-  A.stall_pass = ctx->stall_barrier < 0 ? (int)-ctx->stall_barrier : 0;
+  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
   A.prof = ctx->phase_timing;
   return A;
 }
@@ -2692,8 +2471,7 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   A.part = part;
   A.ctl = ctl;
   A.timeout_ns = ctx->wait_limit_ns;
-  A.stall_barrier = ctx->stall_barrier > 0 ? (unsigned long long)ctx->stall_barrier : 0ull;
-  A.stall_pass = ctx->stall_barrier < 0 ? (int)-ctx->stall_barrier : 0;
+  A.stall_barrier = (unsigned long long)ctx->stall_barrier;
   A.f = f_hat;
   A.tol = tol;
   A.maxit = maxit;

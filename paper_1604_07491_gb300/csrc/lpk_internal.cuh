@@ -55,11 +55,6 @@ struct DevProblem {
   int *seg_c = nullptr;          // [seg_chunks(nnz) + 1]
   double *seg_carry = nullptr;   // [seg_chunks(nnz)]
 
-  // dataflow sweeps (allocated on first use): per CSR entry, the rows of the
-  // previous and next entry of its column in the sweep order (-1: none); a
-  // flag per row
-  int *fl_prev = nullptr, *fl_next = nullptr, *fl_flag = nullptr;
-
   int *color_ptr = nullptr;      // [n_colors+1] device copy
   std::vector<int> color_ptr_h;  // host copy
   std::vector<int> rp_h;         // host copy of rp (sizes the shared-memory row cache)
@@ -116,8 +111,6 @@ struct lpk_ctx {
   int last_resident = 0;         // the last launch cached the rows
   int u_place = 0;               // cluster path: 0 by the problem, 1 u in shared memory, 2 in global memory
   int last_u_global = 0;         // the last cluster launch kept u in global memory
-  int flow_mode = 0;             // grid path sweeps: 0 or 1 a barrier per color, 2 dataflow order
-  int last_flow = 0;             // the last grid launch ordered its sweeps by row flags
   unsigned long long wait_limit_ns = 5000000000ull;  // bound of every grid-barrier wait
   long long stall_barrier = 0;   // testing: grid barrier CTA 0 does not arrive at (0: none)
   int phase_timing = 0;          // persistent kernel: time its barrier intervals by phase kind

@@ -306,7 +306,7 @@ void free_problem(DevProblem &P) {
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
                   P.gm_V,          P.ipm_buf,       P.dcol,      P.cpos,      P.seg_r,     P.seg_c,
-                  P.seg_carry,     P.fl_prev,       P.fl_next,   P.fl_flag};
+                  P.seg_carry};
   for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }

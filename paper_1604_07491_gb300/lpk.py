@@ -23,7 +23,6 @@ STATUS = {0: "OK", 1: "MAX_IPM_ITER", 2: "KRYLOV_STALL", 3: "DIVERGED", 4: "BREA
 MRNE, CGNE, ABGMRES = 0, 1, 2
 EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER, EXEC_BATCH, EXEC_NO_RESIDENT = 0, 1, 2, 3, 4
 EXEC_U_SHARED, EXEC_U_GLOBAL = 8, 16
-EXEC_COLOR_BARRIERS, EXEC_DATAFLOW = 32, 64
 FP64, MIXED = 0, 1
 NE_SSOR, NE_SOR = 0, 1
 
@@ -84,7 +83,7 @@ class Stats(C.Structure):
                 ("csc_passes", C.c_int64), ("barriers", C.c_int64), ("last_cluster_size", C.c_int32),
                 ("last_resident", C.c_int32), ("basis_passes", C.c_int64), ("spmv_launches", C.c_int64),
                 ("spmv_ms", C.c_double), ("phase_ms", C.c_double * 4), ("last_u_global", C.c_int32),
-                ("last_dataflow", C.c_int32), ("tune_probes", C.c_int64), ("tune_cache_hits", C.c_int64)]
+                ("reserved", C.c_int32), ("tune_probes", C.c_int64), ("tune_cache_hits", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "phase_ms"}
@@ -254,10 +253,8 @@ class Context:
         load().lpk_reset_stats(self._h)
 
     def set_wait_limit(self, seconds=5.0, test_stall_barrier=0):
-        """Bound of every grid-barrier and row-flag wait; test_stall_barrier
-        (testing only): k > 0 makes every wait on grid barrier k run out, k < 0
-        every wait on CTA 0's row flags from dataflow pass -k on
-        (lpk_set_wait_limit)."""
+        """Bound of every grid-barrier wait; test_stall_barrier (testing only)
+        makes every wait on that grid barrier run out (lpk_set_wait_limit)."""
         _check(self._h, load().lpk_set_wait_limit(self._h, float(seconds), int(test_stall_barrier)))
 
     def set_phase_timing(self, on=True):
@@ -268,9 +265,7 @@ class Context:
     def set_exec(self, exec_mode=EXEC_AUTO, cluster_size=0):
         """Krylov kernel path: EXEC_AUTO, EXEC_GRID, EXEC_CLUSTER or EXEC_BATCH
         (cluster size 0/2/4/8/16; or-ing EXEC_NO_RESIDENT disables the row cache,
-        EXEC_U_SHARED / EXEC_U_GLOBAL fix where the cluster path keeps u,
-        EXEC_COLOR_BARRIERS / EXEC_DATAFLOW fix how the grid path orders the
-        sweep rows)."""
+        EXEC_U_SHARED / EXEC_U_GLOBAL fix where the cluster path keeps u)."""
         _check(self._h, load().lpk_set_exec(self._h, exec_mode, cluster_size))
 
 
