@@ -349,6 +349,19 @@ void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2) {
   }
   if (P.nnz > 0) LPK_LAUNCH(ctx, k_scale_csc, tblk(P.nnz), TPB, 0, s, P.nnz, P.cpos, P.ah64, P.aht);
 }
+namespace {
+__global__ void k_start_bits(int rows, const int *__restrict__ rp, unsigned *__restrict__ bits) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const int q = rp[r];
+  if (rp[r + 1] > q) atomicOr(bits + (q >> 5), 1u << (q & 31));
+}
+}  // namespace
+
+void start_bits(lpk_ctx *ctx, int rows, const int *rp, unsigned *bits) {
+  if (rows > 0) LPK_LAUNCH(ctx, k_start_bits, tblk(rows), TPB, 0, ctx->stream, rows, rp, bits);
+}
+
 void seg_index(lpk_ctx *ctx, int rows, const int *rp, long long nnz, int *first) {
   const int nw = seg_chunks(nnz);
   LPK_LAUNCH(ctx, k_seg_first, tblk(nw + 1), TPB, 0, ctx->stream, rows, rp, nw, first);

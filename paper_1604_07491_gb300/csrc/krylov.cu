@@ -81,6 +81,14 @@ struct KArgs {
   const float *a32;
   const int *cp, *ri;              // CSC of A_hat (rows are sweep positions)
   const double *aht;               // A_hat values in CSC order
+  // entry-balanced CSC product: chunks of SEG_CH entries (nwc of them), the
+  // first column starting at or after each chunk, the column-start bits and
+  // two partial sums per chunk (see csc_products)
+  const int *seg_c;
+  const unsigned *cbits;
+  double *cstart, *ccont;
+  int nwc;
+  long long nnz;
   int wy;                          // mixed precision: w-space images by FP64 CSC products
   double *uw;                      // n-space workspace of the CGNE wy path
   int ell;
@@ -1029,70 +1037,124 @@ __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, d
   }
 }
 
-// out = A_hat^T x in double through the CSC (thread per column: the columns
-// are short).  Each thread works on CW columns at once (j, j + NT, ...), so
-// the dependent loads column pointer -> row index -> x of different columns
-// are in flight together instead of one column after the other.  Returns this
-// thread's share of ||out||^2 and, if dot_old != nullptr, adds its share of
-// (old, out) where old is read before out is written (old may alias out).
+// out = A_hat^T x in double through the CSC, balanced over entries: the
+// columns follow a power law (mean 6 entries, up to hundreds), so a thread
+// per column leaves most lanes of every FP64 instruction idle and the warp
+// waits for its longest column.  Warp w takes the SEG_CH consecutive CSC
+// entries of chunk w (grid-stride over chunks), lane l the SEG_K from
+// w SEG_CH + l SEG_K.  A lane's multiply-adds run in entry order and restart
+// at each column start (bit q of A.cbits; columns are never empty, so the
+// k-th start of a chunk is column seg_c[w] + k - 1 counted from 1); a column
+// that crosses lanes is combined by a segmented shuffle scan keyed by column,
+// and one that crosses chunks after a group barrier, in chunk order, from
+// the partial sums A.cstart (the chunk where it starts) and A.ccont (the
+// chunks it continues into).  The result does not depend on which warp
+// takes which chunk.  Returns this thread's share of ||out||^2; ok = false
+// if the barrier failed.  Called by every thread of the group.
 template <typename GRP>
-__device__ __forceinline__ double csc_products(const GRP &Gp, const KArgs &A, const double *x, double *out,
-                                               double *dot_old = nullptr) {
-  constexpr int CW = 4;
-  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
+__device__ double csc_products(GRP &Gp, const KArgs &A, const double *x, double *out, int *s_ok, bool &ok) {
+  constexpr int K = SEG_K, CH = SEG_CH;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int gw = Gp.rank() * KWPB + (threadIdx.x >> 5), GW = Gp.size() * KWPB;
+  const long long nnz = A.nnz;
+  auto bit = [&](long long q) -> unsigned { return (__ldg(A.cbits + (q >> 5)) >> (q & 31)) & 1u; };
   double acc = 0.0;
-  for (int j0 = tid; j0 < A.n; j0 += CW * NT) {
-    int q0[CW], q1[CW];
-    double sv[CW];
-    int len = 0;
+  auto finish = [&](int col, double v) {
+    out[col] = v;
+    acc += v * v;
+  };
+  for (int w = gw; w < A.nwc; w += GW) {  // warp-uniform
+    const long long e0 = (long long)w * CH;
+    const int len = (int)(nnz - e0 < CH ? nnz - e0 : CH);
+    const int q0 = lane * K;
+    const int nv = len - q0 < 0 ? 0 : (len - q0 < K ? len - q0 : K);
+    const long long p0 = e0 + q0;
+    int cv[K];
+    double av[K], xv[K];
 #pragma unroll
-    for (int u = 0; u < CW; ++u) {
-      const int j = j0 + u * NT;
-      q0[u] = j < A.n ? __ldg(A.cp + j) : 0;
-      q1[u] = j < A.n ? __ldg(A.cp + j + 1) : 0;
-      len = max(len, q1[u] - q0[u]);
-      sv[u] = 0.0;
-    }
-    // two entries of each of the CW columns per step: their row-index and
-    // value loads, then their gathers, then the multiply-adds in entry order
-    constexpr int TE = 2;
-    for (int t = 0; t < len; t += TE) {
-      int rr[CW][TE];
-      double av[CW][TE], xv[CW][TE];
-#pragma unroll
-      for (int u = 0; u < CW; ++u)
-#pragma unroll
-        for (int e = 0; e < TE; ++e) {
-          const int q = q0[u] + t + e;
-          rr[u][e] = q < q1[u] ? __ldg(A.ri + q) : 0;
-          av[u][e] = q < q1[u] ? __ldg(A.aht + q) : 0.0;
-        }
-#pragma unroll
-      for (int u = 0; u < CW; ++u)
-#pragma unroll
-        for (int e = 0; e < TE; ++e) xv[u][e] = q0[u] + t + e < q1[u] ? ldcg(x + rr[u][e]) : 0.0;
-#pragma unroll
-      for (int u = 0; u < CW; ++u)
-#pragma unroll
-        for (int e = 0; e < TE; ++e)
-          if (q0[u] + t + e < q1[u]) sv[u] += av[u][e] * xv[u][e];
+    for (int j = 0; j < K; ++j) {
+      cv[j] = j < nv ? __ldg(A.ri + p0 + j) : 0;
+      av[j] = j < nv ? __ldg(A.aht + p0 + j) : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < CW; ++u) {
-      const int j = j0 + u * NT;
-      if (j < A.n) {
-        if (dot_old) *dot_old += ldcg(out + j) * sv[u];
-        out[j] = sv[u];
-        acc += sv[u] * sv[u];
+    for (int j = 0; j < K; ++j) xv[j] = j < nv ? ldcg(x + cv[j]) : 0.0;
+    const int ra = __ldg(A.seg_c + w);
+    // bit j: a column starts at entry p0 + j (p0 is a multiple of 8)
+    unsigned b = nv > 0 ? (__ldg(A.cbits + (p0 >> 5)) >> (p0 & 31)) & 0xFFu : 0u;
+    if (nv < K) b &= (1u << nv) - 1u;
+    const bool cont = (__shfl_sync(FULL, b, 0) & 1u) == 0u;  // the column at e0 began earlier
+    const int head_col = cont ? ra - 1 : -1;
+    const int cnt = __popc(b);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int before = incl - cnt;  // column starts in this chunk before the lane's first entry
+    const int incoming = before > 0 ? ra - 1 + before : head_col;
+
+    int cur = incoming, nst = 0;
+    double sv = 0.0, head_part = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      if ((b >> j) & 1u) {
+        if (nst == 0) head_part = sv;  // the incoming column's entries in this lane
+        else finish(cur, sv);          // a column wholly inside this lane
+        ++nst;
+        cur = ra - 1 + before + nst;
+        sv = 0.0;
       }
+      if (j < nv) sv = fma(av[j], xv[j], sv);
     }
+    // segmented inclusive scan of the lanes' last runs, keyed by column
+    const int key = nv > 0 ? cur : -2;
+    double S = sv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double v = __shfl_up_sync(FULL, S, o);
+      const int k = __shfl_up_sync(FULL, key, o);
+      if (lane >= o && k == key) S += v;
+    }
+    const double S_prev = __shfl_up_sync(FULL, S, 1);
+    const int key_prev = __shfl_up_sync(FULL, key, 1);
+    const bool next_starts = __shfl_down_sync(FULL, b & 1u, 1) != 0u;
+    if (nv > 0 && nst > 0 && !(b & 1u) && incoming >= 0) {
+      // the lane ends its incoming column (one that ends at a lane boundary
+      // is ended by the lane before)
+      const double tot = (lane > 0 && key_prev == incoming ? S_prev : 0.0) + head_part;
+      if (cont && incoming == head_col) A.ccont[w] = tot;
+      else finish(incoming, tot);
+    }
+    const bool last_lane = q0 + K >= len;
+    if (nv > 0 && (last_lane || next_starts)) {
+      const bool more = last_lane && e0 + len < nnz && !bit(e0 + len);
+      if (cont && cur == head_col) A.ccont[w] = S;  // no column starts in the chunk before this point
+      else if (more) A.cstart[w] = S;               // goes on in the next chunk
+      else finish(cur, S);
+    }
+  }
+  ok = Gp.sync(s_ok);
+  if (!ok) return acc;
+  // columns that cross chunks: the first chunk that continues a column adds,
+  // in chunk order, its start chunk's and every continuing chunk's sums
+  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
+  for (int w = tid; w < A.nwc; w += NT) {
+    if (w == 0 || bit((long long)w * CH)) continue;
+    const int ra = __ldg(A.seg_c + w);
+    if (__ldg(A.seg_c + w - 1) == ra) continue;  // no column starts in chunk w - 1
+    double v = ldcg(A.cstart + w - 1) + ldcg(A.ccont + w);
+    for (int u = w + 1; u < A.nwc && __ldg(A.seg_c + u) == ra && !bit((long long)u * CH); ++u) v += ldcg(A.ccont + u);
+    finish(ra - 1, v);
   }
   return acc;
 }
 
 // u = -A_hat^T x into the sweep state (u in global memory or in the
 // cluster's shared memory): the starting point of an NR-SOR sweep on
-// min ||A_hat^T y - A_hat^T x||, same column interleaving as csc_products
+// min ||A_hat^T y - A_hat^T x||; a thread per column, CW columns at once
+// (once per BA-GMRES solve, so kept simple)
 template <typename GRP>
 __device__ __forceinline__ void csc_to_u(const GRP &Gp, const KArgs &A, const double *x) {
   constexpr int CW = 4;
@@ -1226,7 +1288,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       double v[1] = {0.0};
       if (A.wy) {
         ++Cn.cols;
-        v[0] = csc_products(Gp, A, A.z, A.q);  // q0 = A_hat^T z in FP64
+        bool ok = true;
+        v[0] = csc_products(Gp, A, A.z, A.q, &s_ok, ok);  // q0 = A_hat^T z in FP64
+        if (!ok) return;
       } else {
         for (int j = tid; j < n; j += NT) {
           double qj = uget(j);
@@ -1297,7 +1361,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         double gnew = w[0];
         if (A.wy) {  // P4: q = A_hat^T qt in FP64, gamma' = ||q||^2
           ++Cn.cols;
-          double w2[1] = {csc_products(Gp, A, A.qt, A.q)};
+          bool ok = true;
+          double w2[1] = {csc_products(Gp, A, A.qt, A.q, &s_ok, ok)};
+          if (!ok) return;
           put_partials<1>(Gp, w2, A.part, sred);
           if (!Gp.sync(&s_ok)) return;
           get_sums<1>(Gp, w2, A.part, sred);
@@ -1382,8 +1448,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         Gp.set_kind(PK_PROD);
         if (A.wy) {  // B = A_hat^T C: w-space image in FP64
           ++Cn.cols;
-          csc_products(Gp, A, A.z, A.uw);
-          if (!Gp.sync(&s_ok)) return;
+          bool ok = true;
+          csc_products(Gp, A, A.z, A.uw, &s_ok, ok);
+          if (!ok || !Gp.sync(&s_ok)) return;
         }
         // v_kk = vin / hs and w = A_hat u / hs on this CTA's rows
         ++Cn.rows;
@@ -1626,8 +1693,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
       gamma = acc[0];
       if (A.wy) {  // u0 = A_hat^T z0 in FP64
         ++Cn.cols;
-        csc_products(Gp, A, A.z, A.uw);
-        if (!Gp.sync(&s_ok)) return;
+        bool ok = true;
+        csc_products(Gp, A, A.z, A.uw, &s_ok, ok);
+        if (!ok || !Gp.sync(&s_ok)) return;
       }
       bool save_best = false;
       while (true) {
@@ -1702,8 +1770,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
         gamma = a2[0];
         if (A.wy) {
           ++Cn.cols;
-          csc_products(Gp, A, A.z, A.uw);
-          if (!Gp.sync(&s_ok)) return;
+          bool ok = true;
+          csc_products(Gp, A, A.z, A.uw, &s_ok, ok);
+          if (!ok || !Gp.sync(&s_ok)) return;
         }
       }
       if (reason != EXIT_CONV && best < gnorm) {
@@ -1716,8 +1785,9 @@ __global__ void __launch_bounds__(KTPB, 1) k_krylov(KArgs A) {
     // ---- explicit residual g = f - A_hat dw; restart when it disagrees ------
     if (A.wy || METH == M_BAG) {  // dw = A_hat^T dy in FP64 keeps the two spaces consistent
       ++Cn.cols;
-      csc_products(Gp, A, A.dy, A.dw);
-      if (!Gp.sync(&s_ok)) return;
+      bool ok = true;
+      csc_products(Gp, A, A.dy, A.dw, &s_ok, ok);
+      if (!ok || !Gp.sync(&s_ok)) return;
     }
     double v[1] = {0.0};
     ++Cn.rows;
@@ -2298,6 +2368,12 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.cp = P.cp;
   A.ri = P.ri;
   A.aht = P.aht;
+  A.seg_c = P.seg_c;
+  A.cbits = P.cbits;
+  A.cstart = P.seg_cstart;
+  A.ccont = P.seg_ccont;
+  A.nwc = seg_chunks(P.nnz);
+  A.nnz = P.nnz;
   A.uw = W.uw;
   A.ell = ell;
   A.omega = omega;
@@ -2462,6 +2538,12 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   A.cp = P.cp;
   A.ri = P.ri;
   A.aht = P.aht;
+  A.seg_c = P.seg_c;
+  A.cbits = P.cbits;
+  A.cstart = P.seg_cstart;
+  A.ccont = P.seg_ccont;
+  A.nwc = seg_chunks(P.nnz);
+  A.nnz = P.nnz;
   A.uw = W.uw;
   A.ell = ell;
   A.omega = omega;

@@ -54,6 +54,11 @@ struct DevProblem {
   int *seg_r = nullptr;          // [seg_chunks(nnz) + 1]
   int *seg_c = nullptr;          // [seg_chunks(nnz) + 1]
   double *seg_carry = nullptr;   // [seg_chunks(nnz)]
+  // the persistent kernel's CSC product (same chunks): bit q of cbits is set
+  // when a column starts at CSC entry q; per chunk, the partial sum of the
+  // column that starts in it and goes on, and of the column it continues
+  unsigned *cbits = nullptr;     // [nnz / 32 + 1]
+  double *seg_cstart = nullptr, *seg_ccont = nullptr;  // [seg_chunks(nnz)]
 
   int *color_ptr = nullptr;      // [n_colors+1] device copy
   std::vector<int> color_ptr_h;  // host copy
@@ -210,6 +215,9 @@ inline int seg_chunks(long long nnz) { return (int)((nnz + SEG_CH - 1) / SEG_CH)
 // first[w] = first of the `rows` compressed rows starting at or after entry
 // w SEG_CH (w < seg_chunks(nnz)), first[seg_chunks(nnz)] = rows
 void seg_index(lpk_ctx *ctx, int rows, const int *rp, long long nnz, int *first);
+// bits[q / 32] bit q % 32 set when one of the `rows` compressed rows starts at
+// entry q (bits zeroed by the caller)
+void start_bits(lpk_ctx *ctx, int rows, const int *rp, unsigned *bits);
 void scale_rows(lpk_ctx *ctx, DevProblem &P, const double *d2);
 void spmv_csr(lpk_ctx *ctx, const DevProblem &P, const double *x, double *y, const double *add,
               double sign);

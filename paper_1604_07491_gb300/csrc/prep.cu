@@ -306,7 +306,7 @@ void free_problem(DevProblem &P) {
                   P.ci,            P.a,             P.src,       P.ah64,      P.ah32,     P.rho,
                   P.cp,            P.ri,            P.at,        P.aht,       P.color_ptr, P.ws,
                   P.gm_V,          P.ipm_buf,       P.dcol,      P.cpos,      P.seg_r,     P.seg_c,
-                  P.seg_carry};
+                  P.seg_carry,     P.cbits,         P.seg_cstart, P.seg_ccont};
   for (void *p : ptrs) dev_free(P.stream, p);
   P = DevProblem();
 }
@@ -505,6 +505,11 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_carry, seg_chunks(nnz)));
   seg_index(ctx, mr, P.rp, nnz, P.seg_r);
   seg_index(ctx, nr, P.cp, nnz, P.seg_c);
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.cbits, nnz / 32 + 1));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_cstart, seg_chunks(nnz)));
+  LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.seg_ccont, seg_chunks(nnz)));
+  LPK_CUDA_TRY(ctx, cudaMemsetAsync(P.cbits, 0, sizeof(unsigned) * (nnz / 32 + 1), st));
+  start_bits(ctx, nr, P.cp, P.cbits);
   // ---- maps to the input numbering ------------------------------------------
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.pos_of_in_row, m));
   LPK_CUDA_TRY(ctx, dev_alloc(ctx, &P.color_in, m));
