@@ -89,6 +89,7 @@ struct KArgs {
   double *cstart, *ccont;
   int nwc;
   long long nnz;
+  int csc_seg;                     // use the entry-balanced CSC product (ragged columns)
   int wy;                          // mixed precision: w-space images by FP64 CSC products
   double *uw;                      // n-space workspace of the CGNE wy path
   int ell;
@@ -1037,10 +1038,69 @@ __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, d
   }
 }
 
-// out = A_hat^T x in double through the CSC, balanced over entries: the
-// columns follow a power law (mean 6 entries, up to hundreds), so a thread
-// per column leaves most lanes of every FP64 instruction idle and the warp
-// waits for its longest column.  Warp w takes the SEG_CH consecutive CSC
+// out = A_hat^T x in double through the CSC, a thread per column, for
+// problems whose columns are short and even (no column much longer than the
+// mean).  Each thread works on CW columns at once (j, j + NT, ...), so the
+// dependent loads column pointer -> row index -> x of different columns are
+// in flight together instead of one column after the other.  Returns this
+// thread's share of ||out||^2.
+template <typename GRP>
+__device__ __forceinline__ double csc_products_cols(const GRP &Gp, const KArgs &A, const double *x, double *out) {
+  constexpr int CW = 4;
+  const int tid = Gp.rank() * blockDim.x + threadIdx.x, NT = Gp.size() * blockDim.x;
+  double acc = 0.0;
+  for (int j0 = tid; j0 < A.n; j0 += CW * NT) {
+    int q0[CW], q1[CW];
+    double sv[CW];
+    int len = 0;
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int j = j0 + u * NT;
+      q0[u] = j < A.n ? __ldg(A.cp + j) : 0;
+      q1[u] = j < A.n ? __ldg(A.cp + j + 1) : 0;
+      len = max(len, q1[u] - q0[u]);
+      sv[u] = 0.0;
+    }
+    // two entries of each of the CW columns per step: their row-index and
+    // value loads, then their gathers, then the multiply-adds in entry order
+    constexpr int TE = 2;
+    for (int t = 0; t < len; t += TE) {
+      int rr[CW][TE];
+      double av[CW][TE], xv[CW][TE];
+#pragma unroll
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e) {
+          const int q = q0[u] + t + e;
+          rr[u][e] = q < q1[u] ? __ldg(A.ri + q) : 0;
+          av[u][e] = q < q1[u] ? __ldg(A.aht + q) : 0.0;
+        }
+#pragma unroll
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e) xv[u][e] = q0[u] + t + e < q1[u] ? ldcg(x + rr[u][e]) : 0.0;
+#pragma unroll
+      for (int u = 0; u < CW; ++u)
+#pragma unroll
+        for (int e = 0; e < TE; ++e)
+          if (q0[u] + t + e < q1[u]) sv[u] += av[u][e] * xv[u][e];
+    }
+#pragma unroll
+    for (int u = 0; u < CW; ++u) {
+      const int j = j0 + u * NT;
+      if (j < A.n) {
+        out[j] = sv[u];
+        acc += sv[u] * sv[u];
+      }
+    }
+  }
+  return acc;
+}
+
+// out = A_hat^T x in double through the CSC, balanced over entries, for
+// ragged columns (a power law: mean 6 entries, up to hundreds), where a
+// thread per column leaves most lanes of every FP64 instruction idle and the
+// warp waits for its longest column.  Warp w takes the SEG_CH consecutive CSC
 // entries of chunk w (grid-stride over chunks), lane l the SEG_K from
 // w SEG_CH + l SEG_K.  A lane's multiply-adds run in entry order and restart
 // at each column start (bit q of A.cbits; columns are never empty, so the
@@ -1052,7 +1112,7 @@ __device__ __forceinline__ void spmv_rows(const GRP &Gp, const KArgs &A, XF x, d
 // takes which chunk.  Returns this thread's share of ||out||^2; ok = false
 // if the barrier failed.  Called by every thread of the group.
 template <typename GRP>
-__device__ double csc_products(GRP &Gp, const KArgs &A, const double *x, double *out, int *s_ok, bool &ok) {
+__device__ double csc_products_seg(GRP &Gp, const KArgs &A, const double *x, double *out, int *s_ok, bool &ok) {
   constexpr int K = SEG_K, CH = SEG_CH;
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -1149,6 +1209,15 @@ __device__ double csc_products(GRP &Gp, const KArgs &A, const double *x, double 
     finish(ra - 1, v);
   }
   return acc;
+}
+
+// out = A_hat^T x: entry-balanced when the columns are ragged (A.csc_seg),
+// else a thread per column; ok = false if a barrier failed
+template <typename GRP>
+__device__ __forceinline__ double csc_products(GRP &Gp, const KArgs &A, const double *x, double *out, int *s_ok,
+                                               bool &ok) {
+  ok = true;
+  return A.csc_seg ? csc_products_seg(Gp, A, x, out, s_ok, ok) : csc_products_cols(Gp, A, x, out);
 }
 
 // u = -A_hat^T x into the sweep state (u in global memory or in the
@@ -2374,6 +2443,7 @@ KArgs base_args(lpk_ctx *ctx, DevProblem &P, Workspace &W, int ell, double omega
   A.ccont = P.seg_ccont;
   A.nwc = seg_chunks(P.nnz);
   A.nnz = P.nnz;
+  A.csc_seg = P.ragged_cols;
   A.uw = W.uw;
   A.ell = ell;
   A.omega = omega;
@@ -2544,6 +2614,7 @@ lpk_status krylov_solve_scratch(lpk_ctx *ctx, DevProblem &P, int method, int pre
   A.ccont = P.seg_ccont;
   A.nwc = seg_chunks(P.nnz);
   A.nnz = P.nnz;
+  A.csc_seg = P.ragged_cols;
   A.uw = W.uw;
   A.ell = ell;
   A.omega = omega;

@@ -58,6 +58,7 @@ struct DevProblem {
   // when a column starts at CSC entry q; per chunk, the partial sum of the
   // column that starts in it and goes on, and of the column it continues
   unsigned *cbits = nullptr;     // [nnz / 32 + 1]
+  int ragged_cols = 0;           // longest column >= 32 entries and > 4 x the mean: entry-balanced CSC
   double *seg_cstart = nullptr, *seg_ccont = nullptr;  // [seg_chunks(nnz)]
 
   int *color_ptr = nullptr;      // [n_colors+1] device copy

@@ -518,7 +518,12 @@ lpk_status prep_problem(lpk_ctx *ctx, const lpk_matrix *A, uint64_t seed, DevPro
   if (mr > 0) LPK_LAUNCH(ctx, k_inrow_of_pos, nblk(mr), TPB, 0, st, mr, perm, red_row, P.in_row_of_pos);
   P.rp_h.assign(mr + 1, 0);
   LPK_CUDA_TRY(ctx, cudaMemcpyAsync(P.rp_h.data(), P.rp, sizeof(int) * (mr + 1), cudaMemcpyDeviceToHost, st));
+  std::vector<int> cp_h(nr + 1, 0);
+  LPK_CUDA_TRY(ctx, cudaMemcpyAsync(cp_h.data(), P.cp, sizeof(int) * (nr + 1), cudaMemcpyDeviceToHost, st));
   LPK_CUDA_TRY(ctx, cudaGetLastError());
   LPK_CUDA_TRY(ctx, ctx_sync(ctx));
+  int max_col = 0;
+  for (int j = 0; j < nr; ++j) max_col = std::max(max_col, cp_h[j + 1] - cp_h[j]);
+  P.ragged_cols = nr > 0 && max_col >= 32 && (double)max_col > 4.0 * (double)nnz / nr;
   return LPK_OK;
 }
